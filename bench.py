@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused DPF EvalAll + dpXOR server path (IM-PIR §3, Algorithm 1) on one GB300.
+
+Workload (default): the 8 GiB uneven batch workload: N = 2^25 records x 256 B (8 GiB,
+uniform random bytes), 1024 queries split into batches of uniform random size 1..512 whose
+keys mix domain sizes 2^23, 2^24 and 2^25 (each against the DB prefix it covers). One step
+answers all 1024 queries (one server's keys), batch after batch, each batch one persistent
+fused launch. The DB (8 GiB) is larger than L2 (129 MB), so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. `value` is device-timed queries/s with keys already in HBM; `e2e`
+is the same metric through the synchronous C-ABI call with host buffers (key upload and
+answer download inside the timed region). Under torchrun each rank answers its own copy of
+the workload (independent batches: weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = ("uneven8g", "batched4g", "batched256m", "single")
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=WORKLOADS, default="uneven8g")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-plain", action="store_true", help="skip the one-query-per-launch comparison")
+    p.add_argument("--no-tune", action="store_true")
+    p.add_argument("--cpu-sample", type=int, default=2, help="queries in the oracle's timed sample")
+    return p.parse_args()
+
+
+def make_workload(name):
+    from paper_2509_06514_gb300 import workloads as W
+    return {"uneven8g": W.uneven_8gib, "batched4g": W.batched_4gib, "batched256m": W.batched_256mib,
+            "single": W.single_query}[name]()
+
+
+# ---------------------------------------------------------------- distributed plumbing
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks during the timed region
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for ln in fh:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = max((num(r[2]) or 0) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        loaded = [s for s in sm if s > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": mx,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0) for r in rows)}
+
+
+# ---------------------------------------------------------------- algorithmic work
+
+def aes_blocks(m: int) -> int:
+    """AES-128 encryptions of one full-domain evaluation: 2 (2^m - 1) (one per tree edge)."""
+    return 2 * ((1 << m) - 1)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# Lookups the T-table formulation needs per AES-128 block of the keyed PRF: 16 per round for
+# 10 rounds plus the key schedule's 4 per round shared by the two children of a node.
+LOOKUPS_PER_BLOCK_KEYED = 160 + 20
+SMEM_LOOKUPS_PER_CLK_PER_SM = 32   # one 32-bit word per bank per clock, 32 banks
+
+
+def aes_peak_gaes(sms: int, mhz: float) -> float:
+    return sms * mhz * 1e6 * SMEM_LOOKUPS_PER_CLK_PER_SM / LOOKUPS_PER_BLOCK_KEYED / 1e9
+
+
+# ---------------------------------------------------------------- reference arm: the CPU oracle
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2509_06514_gb300 import workloads
+    oracle.build()
+    w = make_workload(args.workload)
+    cores = os.cpu_count() or 1
+    b0 = w.batches[0]
+    # one query per step, taken round-robin from the workload (records regenerated once)
+    db = workloads.make_db(w.n_records, w.record_bytes, w.db_seed)
+    qs = [(m, a, s) for b in w.batches for m, a, s in zip(b.ms, b.alphas, b.seeds)]
+    times = []
+    for i in range(args.warmup + args.steps):
+        m, a, s = qs[i % len(qs)]
+        k0, _ = oracle.gen(a, m, oracle.PRF_KEYED, s)
+        t0 = time.perf_counter()
+        oracle.answer(k0, db, w.n_records, w.record_bytes, threads=cores)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    del b0
+    total = sum(times)
+    v = args.steps / total
+    print(json.dumps({
+        "impl": "reference", "metric": "PIR queries/s (DPF eval+dpXOR) at 8 GiB DB", "value": v,
+        "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded uniform random records)",
+        "config": {"workload": w.name, "step": "one query of the workload per step (bounded sample)"},
+        "cpu_baseline": {"value": v, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} queries of the workload, one per step, threaded oracle"},
+        "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    import paper_2509_06514_gb300 as impir
+    from paper_2509_06514_gb300 import build, workloads
+
+    torch.cuda.set_device(local)
+    build.build()
+    w = make_workload(args.workload)
+    N, B = w.n_records, w.record_bytes
+    t_setup = time.perf_counter()
+    db = workloads.make_db(N, B, w.db_seed)
+    dbh = impir.impir_db_load(db, N, B)
+    stride = impir.impir_db_info(dbh)["stride_bytes"]
+    sms = impir.impir_device_sm_count()
+
+    # keys of both servers for every query (client side, outside any timed region)
+    batches = []
+    for b in w.batches:
+        k0s, k1s = [], []
+        for m, a, s in zip(b.ms, b.alphas, b.seeds):
+            k0, k1 = impir.dpf_gen(a, m, impir.IMPIR_PRF_AES_KEYED, s)
+            k0s.append(k0)
+            k1s.append(k1)
+        n = len(k0s)
+        blob0, offs = impir.pack_keys(k0s)
+        blob1, _ = impir.pack_keys(k1s)
+        wsb = impir.impir_workspace_bytes(n, stride)
+        batches.append({
+            "n": n, "ms": list(b.ms), "alphas": list(b.alphas), "blob0": blob0, "blob1": blob1,
+            "d_keys0": torch.from_numpy(np.frombuffer(blob0, np.uint8).copy()).cuda(),
+            "d_keys1": torch.from_numpy(np.frombuffer(blob1, np.uint8).copy()).cuda(),
+            "d_off": torch.from_numpy(offs.view(np.int32).copy()).cuda(),
+            "d_out": torch.zeros((n, B), dtype=torch.uint8, device="cuda"),
+            "d_ws": torch.empty(wsb, dtype=torch.uint8, device="cuda"), "wsb": wsb,
+        })
+    nq = sum(bt["n"] for bt in batches)
+    stream = torch.cuda.Stream()
+
+    def run_step(server=0):
+        for bt in batches:
+            impir.impir_answer_async(dbh, bt["d_keys%d" % server], bt["d_off"], bt["n"], bt["d_out"], bt["d_ws"],
+                                     bt["wsb"], stream)
+
+    # autotune on the largest batch (outside the timed region)
+    tuned = None
+    if not args.no_tune:
+        big = max(batches, key=lambda bt: bt["n"])
+        tuned = impir.impir_autotune(dbh, big["d_keys0"], big["d_off"], big["n"], big["d_out"], big["d_ws"],
+                                     big["wsb"], stream).as_dict()
+    cfg = impir.impir_get_config(dbh).as_dict()
+
+    # parity on the GPU answers of this run: both servers, reconstruction of every query
+    run_step(1)
+    stream.synchronize()
+    ans1 = [bt["d_out"].cpu().numpy().copy() for bt in batches]
+    run_step(0)
+    stream.synchronize()
+    ans0 = [bt["d_out"].cpu().numpy().copy() for bt in batches]
+    bad = 0
+    for bt, a0, a1 in zip(batches, ans0, ans1):
+        for i, (m, a) in enumerate(zip(bt["ms"], bt["alphas"])):
+            want = db[a] if a < N else np.zeros(B, np.uint8)
+            bad += int(not np.array_equal(a0[i] ^ a1[i], want))
+    setup_s = time.perf_counter() - t_setup
+
+    for _ in range(args.warmup):
+        run_step()
+    stream.synchronize()
+
+    # ---- device-timed region: keys resident in HBM ----
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    impir.impir_timing_enable(True)
+    with Clocks(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            run_step()
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        barrier(world)
+    fused_ms, fused_launches, all_launches = impir.impir_timing_read()
+    impir.impir_timing_enable(False)
+    ms = max_over_ranks(world, e0.elapsed_time(e1))
+    clocks = clk.summary()
+    value = nq * args.steps * world / (ms / 1e3)
+
+    # ---- e2e: the synchronous C-ABI call with host buffers (H2D keys, D2H answers inside) ----
+    h2d = sum(len(bt["blob0"]) + 4 * bt["n"] for bt in batches)
+    d2h = nq * B
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for bt in batches:
+            impir.impir_answer(dbh, bt["blob0"], bt["n"], B)
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    e2e = {"value": nq * args.steps * world / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+
+    # ---- plain form: one query per launch on the same queries ----
+    plain = None
+    if not args.no_plain:
+        impir.impir_set_config(dbh, cfg["lane_bits"], 1, cfg["warps_per_cta"], 1)
+        pc = impir.impir_get_config(dbh).as_dict()
+        run_step()
+        stream.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        run_step()
+        p1.record(stream)
+        p1.synchronize()
+        pms = p0.elapsed_time(p1)
+        same = all(np.array_equal(bt["d_out"].cpu().numpy(), a) for bt, a in zip(batches, ans0))
+        plain = {"value": nq / (pms / 1e3), "unit": "queries/s", "config": pc, "bit_identical_to_batched": same}
+        impir.impir_set_config(dbh, cfg["lane_bits"], cfg["queries_per_warp"], cfg["warps_per_cta"], 0)
+
+    # ---- roofline of the dominant kernel (fused EvalAll + dpXOR) ----
+    pk, pk_kind = peaks()
+    mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    blocks_per_step = sum(aes_blocks(m) for bt in batches for m in bt["ms"])
+    launch_ms = fused_ms / max(1, fused_launches)
+    achieved = blocks_per_step * args.steps / (fused_ms / 1e3) / 1e9 if fused_ms else None
+    peak = aes_peak_gaes(sms, mhz)
+    scan_bytes = sum(min(N, 1 << m) * B for bt in batches for m in bt["ms"])
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cores = os.cpu_count() or 1
+        qs = [(bi, i) for bi, bt in enumerate(batches) for i in range(bt["n"])][: args.cpu_sample]
+        t0 = time.perf_counter()
+        agree = True
+        for bi, i in qs:
+            bt = batches[bi]
+            key = bt["blob0"][:0]
+            k0, _ = impir.pack_keys([]) if False else (None, None)
+            o = 0
+            for j in range(i):
+                o += impir.impir_key_bytes(bt["ms"][j])
+            key = bt["blob0"][o:o + impir.impir_key_bytes(bt["ms"][i])]
+            r = oracle.answer(key, db, N, B, threads=cores)
+            agree &= r == ans0[bi][i].tobytes()
+        dt = time.perf_counter() - t0
+        cpu = {"value": len(qs) / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
+               "sample": f"{len(qs)} queries of the workload (m={[batches[b]['ms'][i] for b, i in qs]}), "
+                         f"threaded oracle, {dt:.1f} s", "bit_identical_to_gpu": bool(agree)}
+
+    if rank == 0:
+        out = {
+            "metric": "PIR queries/s (DPF eval+dpXOR) at 8 GiB DB", "value": value, "unit": "queries/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic (seeded uniform random records; keys from the library's Gen)",
+            "config": {"workload": w.name, "queries_per_step": nq, "batches": [bt["n"] for bt in batches],
+                       "db_bytes": N * B, "record_bytes": B, "l2": "DB (8 GiB) larger than L2, no flush",
+                       "prf": "AES-128 keyed by the node seed (paper's PRF)", "launch": cfg, "tuned": tuned},
+            "e2e": e2e,
+            "gpu_launches": all_launches,
+            "clocks": clocks,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GAES/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "peak_basis": f"{sms} SMs x {mhz:.0f} MHz x {SMEM_LOOKUPS_PER_CLK_PER_SM} table lookups/clk"
+                                       f" / {LOOKUPS_PER_BLOCK_KEYED} lookups per keyed AES block",
+                         "kernel": "fused_kernel", "avg_launch_ms": launch_ms, "launches": fused_launches},
+            "scan": {"logical_gbs": scan_bytes * args.steps / (ms / 1e3) / 1e9, "hbm_peak_gbs": pk.get("hbm_gbs"),
+                     "peak_kind": pk_kind},
+            "aes_blocks_per_s": blocks_per_step * args.steps / (ms / 1e3),
+            "one_query_per_launch": plain,
+            "parity": {"reconstructed_ok": nq - bad, "queries": nq},
+            "cpu_baseline": cpu,
+            "setup_s": setup_s,
+        }
+        print(json.dumps(out), flush=True)
+    impir.impir_db_free(dbh)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * impir.h — C ABI of the GB300 server side of two-server DPF-based PIR (IM-PIR,
+ * arXiv 2509.06514): full-domain DPF evaluation fused with dpXOR on one GPU.
+ *
+ * Conventions for every call below:
+ *   - Every call returns an impir_status; nothing throws across this boundary.
+ *     On failure impir_last_error() gives a thread-local message.
+ *   - The caller owns every buffer it passes. The library owns a database's device
+ *     copy from impir_db_load until impir_db_free (impir_db_attach borrows instead).
+ *   - "Host" pointers are ordinary CPU memory; "device" pointers are CUDA global memory
+ *     of the current device (for example a torch CUDA tensor's data_ptr()).
+ *   - Synchronous calls return only after their outputs are written.
+ *
+ * Key wire format (little-endian), the DPF key of §3.1: two codewords
+ * C_0, C_1 in F_{2^128}^{2 x (m+1)}.
+ *   byte 0   version, must be IMPIR_KEY_VERSION (1)
+ *   byte 1   prf, an impir_prf
+ *   byte 2   m, the domain bits, 1..IMPIR_MAX_DOMAIN_BITS; the domain is 2^m leaves
+ *   bytes 3..7 zero
+ *   then C_0[2][m+1][16] and C_1[2][m+1][16]: [row = child bit x][column = depth d].
+ *   Column 0 holds only the root seed C_0[0][0]; C_0[1][0], C_1[0][0] and C_1[1][0]
+ *   must be zero. Total impir_key_bytes(m) = 8 + 64 (m + 1) bytes.
+ *
+ * A key with domain bits m is answered over records [0, min(2^m, N)): leaves j >= N
+ * select nothing, and a key with 2^m < N covers the DB prefix its domain spans.
+ */
+#ifndef IMPIR_H
+#define IMPIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IMPIR_OK = 0,
+    IMPIR_EINVAL = 1,   /* malformed argument or key; nothing was launched */
+    IMPIR_ENOMEM = 2,   /* host or device allocation failed, or a workspace is too small */
+    IMPIR_ECUDA = 3,    /* a CUDA runtime call failed (no device, launch error, ...) */
+    IMPIR_ETIMEOUT = 4, /* a bounded wait gave up (serving loop) */
+    IMPIR_EBUSY = 5     /* the resource is in use (for example a DB with queries in flight) */
+} impir_status;
+
+/* The PRF of Eq. (3). The paper's PRF_s(x) "encrypts x with key s" (§3.2): AES-128 keyed
+ * by the 128-bit parent seed s over the block enc(x) (byte 0 = x, other bytes 0).
+ * IMPIR_PRF_AES_MMO is the fixed-key alternative PRF_s(x) = AES_{K_x}(s) XOR s with the
+ * two fixed keys below (Matyas-Meyer-Oseas). */
+typedef enum { IMPIR_PRF_AES_KEYED = 0, IMPIR_PRF_AES_MMO = 1 } impir_prf;
+
+#define IMPIR_KEY_VERSION 1
+#define IMPIR_MAX_DOMAIN_BITS 40
+/* K_0 and K_1 of IMPIR_PRF_AES_MMO: the ASCII strings "IM-PIR MMO key 0" / "... 1". */
+#define IMPIR_MMO_KEY0 "IM-PIR MMO key 0"
+#define IMPIR_MMO_KEY1 "IM-PIR MMO key 1"
+
+/* Size in bytes of one key with domain bits m: 8 + 64 (m + 1). */
+size_t impir_key_bytes(uint32_t m);
+
+/* ---- Database (§3.3 "Database preloading": copied once, resident, not timed) ---- */
+
+/* Copies n_records records of record_bytes each from host memory `records` (row-major,
+ * contiguous) into device memory owned by the library, padding each record to a
+ * 16-byte-aligned stride with zero bytes. On success *db_handle names the database.
+ * EINVAL: records NULL, n_records 0, record_bytes 0, or n_records > 2^40.
+ * ENOMEM: the device allocation failed. */
+impir_status impir_db_load(const void* records, uint64_t n_records, uint32_t record_bytes, int32_t* db_handle);
+
+/* Registers a database that already lives in device memory (for example a torch tensor):
+ * record j starts at d_records + j * stride_bytes. stride_bytes must be a multiple of 16
+ * and >= record_bytes, d_records 16-byte aligned, and the padding bytes of every record
+ * must be zero. The library does not copy or free it; it must outlive the handle. */
+impir_status impir_db_attach(const void* d_records, uint64_t n_records, uint32_t record_bytes,
+                             uint32_t stride_bytes, int32_t* db_handle);
+
+/* Releases the handle (and the device copy if impir_db_load made it). EINVAL: unknown handle. */
+impir_status impir_db_free(int32_t db_handle);
+
+/* Describes a database: record count, record bytes, device stride and device pointer. */
+impir_status impir_db_info(int32_t db_handle, uint64_t* n_records, uint32_t* record_bytes, uint32_t* stride_bytes,
+                           const void** d_records);
+
+/* ---- Answering (Algorithm 1: EvaluateDPF + TaskletXOR + MasterXOR + Aggregate) ---- */
+
+/* Answers n_queries keys against one database: for each key k,
+ *   out[q] = XOR over j < min(N, 2^m) of lsb(Eval(k, j)) * D[j]          (§2.3, §3.3)
+ * with Eval(k, j) = R(m, j) of Eqs. (1)-(3). `keys` is host memory holding the n_queries
+ * keys back to back (each impir_key_bytes(m) long, m read from its header; keys of
+ * different m may be mixed). `out` is host memory of n_queries * record_bytes bytes.
+ * All keys are validated before any launch: one malformed key gives EINVAL and no output.
+ * The keys go to the device, one batched fused launch answers all of them, and the
+ * answers come back; the call returns when `out` is written. */
+impir_status impir_answer(int32_t db_handle, const uint8_t* keys, uint32_t n_queries, uint8_t* out);
+
+/* Device workspace an asynchronous answer of n_queries keys against a database of
+ * record stride stride_bytes needs (bytes). */
+size_t impir_workspace_bytes(uint32_t n_queries, uint32_t stride_bytes);
+
+/* Asynchronous form on a caller stream with caller-owned device memory; it allocates
+ * nothing and never synchronizes, so it can be captured into a CUDA graph.
+ *   d_keys         device, the keys back to back
+ *   d_key_offsets  device, n_queries uint32 byte offsets of each key inside d_keys
+ *   d_out          device, n_queries * record_bytes bytes, written
+ *   d_workspace    device, >= impir_workspace_bytes(n_queries, stride), 256-byte aligned
+ *   cuda_stream    a cudaStream_t (NULL = the legacy default stream)
+ * Keys are validated on the device: a malformed key's answer is all zero and the first
+ * such query index is recorded; read it with impir_workspace_status after the stream
+ * completes. Launch errors return ECUDA. */
+impir_status impir_answer_async(int32_t db_handle, const uint8_t* d_keys, const uint32_t* d_key_offsets,
+                                uint32_t n_queries, uint8_t* d_out, void* d_workspace, size_t workspace_bytes,
+                                void* cuda_stream);
+
+/* Reads the device-side status of the last asynchronous answer that used d_workspace
+ * (synchronizes with the device). *n_bad = number of malformed keys, *first_bad = the
+ * smallest index among them (UINT32_MAX when none). */
+impir_status impir_workspace_status(const void* d_workspace, uint32_t* n_bad, uint32_t* first_bad);
+
+/* ---- Launch configuration and autotuning ---- */
+
+/* Shape of the fused launch (the GPU analog of the paper's tasklets, DPU clusters and
+ * subtree split, §3.2-§3.4):
+ *   lane_bits          each lane expands a perfect subtree of 2^lane_bits leaves
+ *                      (a warp tile is 32 * 2^lane_bits records); 0..10
+ *   queries_per_warp   queries evaluated per warp tile before one shared scan of the
+ *                      tile (1, 2, 4 or 8): the DB tile is read once for all of them
+ *   warps_per_cta      4..16
+ *   queries_per_launch 0 = the whole batch in one persistent launch; 1 = the plain
+ *                      one-query-per-launch form (one launch per key, in order) */
+typedef struct {
+    uint32_t lane_bits;
+    uint32_t queries_per_warp;
+    uint32_t warps_per_cta;
+    uint32_t queries_per_launch;
+} impir_config;
+
+/* Gets or sets the configuration used for a database (set validates it: EINVAL). */
+impir_status impir_get_config(int32_t db_handle, impir_config* cfg);
+impir_status impir_set_config(int32_t db_handle, const impir_config* cfg);
+
+/* Times candidate configurations on the given asynchronous problem (same arguments as
+ * impir_answer_async, which it runs repeatedly on cuda_stream), keeps the fastest for
+ * this database, writes it to *best and records it in the process-wide tuning cache
+ * keyed by (SM count, N, stride, batch size, largest m). Synchronizes the stream. */
+impir_status impir_autotune(int32_t db_handle, const uint8_t* d_keys, const uint32_t* d_key_offsets,
+                            uint32_t n_queries, uint8_t* d_out, void* d_workspace, size_t workspace_bytes,
+                            void* cuda_stream, impir_config* best);
+
+/* ---- Client side, used by tests (§3.1 Gen, §2.3 reconstruction) ---- */
+
+/* Gen(alpha) for domain bits m: writes key0 and key1 (impir_key_bytes(m) each) such that
+ * Eval(key0, j) XOR Eval(key1, j) is the 128-bit integer 1 at j = alpha and 0 elsewhere.
+ * Randomness: SplitMix64 seeded with the XOR of the four little-endian 64-bit words of
+ * rng_seed (draw order: the two roots, then per depth and child bit a uniform codeword
+ * and, on the path above the leaves, a uniform offset with lsb 1).
+ * EINVAL: m outside 1..40, alpha >= 2^m, unknown prf, NULL buffers. */
+impir_status dpf_gen(uint64_t alpha, uint32_t m, impir_prf prf, const uint8_t rng_seed[32], uint8_t* key0,
+                     uint8_t* key1);
+
+/* D[i] = r0 XOR r1 (§2.3): the client combines the two servers' answers. */
+impir_status impir_reconstruct(const uint8_t* r0, const uint8_t* r1, uint32_t record_bytes, uint8_t* out);
+
+/* Thread-local message describing the last failure on this thread ("" if none). */
+const char* impir_last_error(void);
+
+/* ---- Kernel timing (measurement support; off by default) ----
+ * While enabled, each fused EvalAll + dpXOR launch is bracketed by two CUDA events recorded
+ * on the stream it is launched on. impir_timing_read waits for those events and returns the
+ * summed device time of the fused launches (milliseconds), their count, and the count of
+ * every kernel the library launched (setup, fused, finalize) since the last enable.
+ * Do not enable it while a stream is being captured into a CUDA graph. */
+impir_status impir_timing_enable(int enable);
+impir_status impir_timing_read(double* fused_ms, uint64_t* fused_launches, uint64_t* all_launches);
+
+/* Number of streaming multiprocessors of the current device (0 if none). */
+int32_t impir_device_sm_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IMPIR_H */

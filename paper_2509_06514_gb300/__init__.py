@@ -1,0 +1,253 @@
+"""GB300 server side of two-server DPF-based PIR (IM-PIR, arXiv 2509.06514).
+
+A thin ctypes binding over ``libimpir.so`` (C ABI in ``include/impir.h``). Every call has
+the C name and only marshals arguments; every step of the answer path runs in the
+library's CUDA kernels. There is no CPU fallback: if the library is missing or no CUDA
+device is present, calls raise.
+
+Host buffers are ``bytes`` / numpy uint8 arrays; device buffers are torch CUDA tensors
+(torch supplies device memory and streams) or raw integer device pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libimpir.so")
+
+IMPIR_OK, IMPIR_EINVAL, IMPIR_ENOMEM, IMPIR_ECUDA, IMPIR_ETIMEOUT, IMPIR_EBUSY = range(6)
+IMPIR_PRF_AES_KEYED = 0
+IMPIR_PRF_AES_MMO = 1
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUSY"}
+
+# Every symbol include/impir.h declares.
+EXPORTS = [
+    "impir_key_bytes", "impir_db_load", "impir_db_attach", "impir_db_free", "impir_db_info", "impir_answer",
+    "impir_workspace_bytes", "impir_answer_async", "impir_workspace_status", "impir_get_config",
+    "impir_set_config", "impir_autotune", "dpf_gen", "impir_reconstruct", "impir_last_error",
+    "impir_device_sm_count", "impir_timing_enable", "impir_timing_read",
+]
+
+
+class ImpirError(RuntimeError):
+    def __init__(self, status: int, what: str, message: str):
+        super().__init__(f"{what}: {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class impir_config(ctypes.Structure):
+    _fields_ = [("lane_bits", ctypes.c_uint32), ("queries_per_warp", ctypes.c_uint32),
+                ("warps_per_cta", ctypes.c_uint32), ("queries_per_launch", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded libimpir.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"libimpir.so is not built ({LIB_PATH}); run __graft_entry__.build() or "
+                                  "python -m paper_2509_06514_gb300.build")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, u8p = ctypes.c_void_p, ctypes.c_void_p
+            sig = {
+                "impir_key_bytes": (ctypes.c_size_t, [ctypes.c_uint32]),
+                "impir_db_load": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32)]),
+                "impir_db_attach": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                                   ctypes.POINTER(ctypes.c_int32)]),
+                "impir_db_free": (ctypes.c_int, [ctypes.c_int32]),
+                "impir_db_info": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64),
+                                                 ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                                                 ctypes.POINTER(ctypes.c_void_p)]),
+                "impir_answer": (ctypes.c_int, [ctypes.c_int32, u8p, ctypes.c_uint32, u8p]),
+                "impir_workspace_bytes": (ctypes.c_size_t, [ctypes.c_uint32, ctypes.c_uint32]),
+                "impir_answer_async": (ctypes.c_int, [ctypes.c_int32, vp, vp, ctypes.c_uint32, vp, vp,
+                                                      ctypes.c_size_t, vp]),
+                "impir_workspace_status": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_uint32),
+                                                          ctypes.POINTER(ctypes.c_uint32)]),
+                "impir_get_config": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(impir_config)]),
+                "impir_set_config": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(impir_config)]),
+                "impir_autotune": (ctypes.c_int, [ctypes.c_int32, vp, vp, ctypes.c_uint32, vp, vp, ctypes.c_size_t,
+                                                  vp, ctypes.POINTER(impir_config)]),
+                "dpf_gen": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, u8p, u8p, u8p]),
+                "impir_reconstruct": (ctypes.c_int, [u8p, u8p, ctypes.c_uint32, u8p]),
+                "impir_last_error": (ctypes.c_char_p, []),
+                "impir_device_sm_count": (ctypes.c_int32, []),
+                "impir_timing_enable": (ctypes.c_int, [ctypes.c_int]),
+                "impir_timing_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64),
+                                                     ctypes.POINTER(ctypes.c_uint64)]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype, f.argtypes = res, args
+            _lib = L
+    return _lib
+
+
+def _check(st: int, what: str) -> None:
+    if st != IMPIR_OK:
+        raise ImpirError(st, what, lib().impir_last_error().decode(errors="replace"))
+
+
+def _host(buf) -> tuple[np.ndarray, ctypes.c_void_p]:
+    a = np.frombuffer(buf, dtype=np.uint8) if isinstance(buf, (bytes, bytearray, memoryview)) else \
+        np.ascontiguousarray(buf, dtype=np.uint8)
+    return a, ctypes.c_void_p(a.ctypes.data)
+
+
+def _dev(x) -> ctypes.c_void_p:
+    """Device pointer of a torch CUDA tensor, or an integer pointer."""
+    if x is None:
+        return ctypes.c_void_p(0)
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        return ctypes.c_void_p(x.data_ptr())
+    raise TypeError(f"not a device buffer: {type(x)}")
+
+
+def _stream(s) -> ctypes.c_void_p:
+    if s is None:
+        return ctypes.c_void_p(0)
+    if isinstance(s, int):
+        return ctypes.c_void_p(s)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ---- C ABI, same names ----
+
+def impir_key_bytes(m: int) -> int:
+    return int(lib().impir_key_bytes(m))
+
+
+def impir_db_load(records, n_records: int, record_bytes: int) -> int:
+    arr, p = _host(records)
+    assert arr.size >= n_records * record_bytes
+    h = ctypes.c_int32(0)
+    _check(lib().impir_db_load(p, n_records, record_bytes, ctypes.byref(h)), "impir_db_load")
+    return h.value
+
+
+def impir_db_attach(d_records, n_records: int, record_bytes: int, stride_bytes: int) -> int:
+    h = ctypes.c_int32(0)
+    _check(lib().impir_db_attach(_dev(d_records), n_records, record_bytes, stride_bytes, ctypes.byref(h)),
+           "impir_db_attach")
+    return h.value
+
+
+def impir_db_free(db: int) -> None:
+    _check(lib().impir_db_free(db), "impir_db_free")
+
+
+def impir_db_info(db: int) -> dict:
+    n, b, s, d = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_void_p()
+    _check(lib().impir_db_info(db, ctypes.byref(n), ctypes.byref(b), ctypes.byref(s), ctypes.byref(d)),
+           "impir_db_info")
+    return {"n_records": n.value, "record_bytes": b.value, "stride_bytes": s.value, "d_records": d.value}
+
+
+def impir_answer(db: int, keys, n_queries: int, record_bytes: int) -> np.ndarray:
+    """Synchronous answer of n_queries host keys; returns (n_queries, record_bytes) uint8."""
+    _, kp = _host(keys)
+    out = np.zeros((n_queries, record_bytes), np.uint8)
+    _check(lib().impir_answer(db, kp, n_queries, ctypes.c_void_p(out.ctypes.data)), "impir_answer")
+    return out
+
+
+def impir_workspace_bytes(n_queries: int, stride_bytes: int) -> int:
+    return int(lib().impir_workspace_bytes(n_queries, stride_bytes))
+
+
+def impir_answer_async(db: int, d_keys, d_key_offsets, n_queries: int, d_out, d_workspace, workspace_bytes: int,
+                       stream=None) -> None:
+    _check(lib().impir_answer_async(db, _dev(d_keys), _dev(d_key_offsets), n_queries, _dev(d_out),
+                                    _dev(d_workspace), workspace_bytes, _stream(stream)), "impir_answer_async")
+
+
+def impir_workspace_status(d_workspace) -> tuple[int, int]:
+    nb, fb = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().impir_workspace_status(_dev(d_workspace), ctypes.byref(nb), ctypes.byref(fb)),
+           "impir_workspace_status")
+    return nb.value, fb.value
+
+
+def impir_get_config(db: int) -> impir_config:
+    c = impir_config()
+    _check(lib().impir_get_config(db, ctypes.byref(c)), "impir_get_config")
+    return c
+
+
+def impir_set_config(db: int, lane_bits: int, queries_per_warp: int, warps_per_cta: int = 16,
+                     queries_per_launch: int = 0) -> None:
+    c = impir_config(lane_bits, queries_per_warp, warps_per_cta, queries_per_launch)
+    _check(lib().impir_set_config(db, ctypes.byref(c)), "impir_set_config")
+
+
+def impir_autotune(db: int, d_keys, d_key_offsets, n_queries: int, d_out, d_workspace, workspace_bytes: int,
+                   stream=None) -> impir_config:
+    c = impir_config()
+    _check(lib().impir_autotune(db, _dev(d_keys), _dev(d_key_offsets), n_queries, _dev(d_out), _dev(d_workspace),
+                                workspace_bytes, _stream(stream), ctypes.byref(c)), "impir_autotune")
+    return c
+
+
+def dpf_gen(alpha: int, m: int, prf: int, rng_seed: bytes) -> tuple[bytes, bytes]:
+    assert len(rng_seed) == 32
+    kb = impir_key_bytes(m)
+    k0, k1 = np.zeros(kb, np.uint8), np.zeros(kb, np.uint8)
+    _, sp = _host(rng_seed)
+    _check(lib().dpf_gen(alpha, m, prf, sp, ctypes.c_void_p(k0.ctypes.data), ctypes.c_void_p(k1.ctypes.data)),
+           "dpf_gen")
+    return k0.tobytes(), k1.tobytes()
+
+
+def impir_reconstruct(r0, r1) -> bytes:
+    a, pa = _host(r0)
+    _, pb = _host(r1)
+    out = np.zeros(a.size, np.uint8)
+    _check(lib().impir_reconstruct(pa, pb, a.size, ctypes.c_void_p(out.ctypes.data)), "impir_reconstruct")
+    return out.tobytes()
+
+
+def impir_last_error() -> str:
+    return lib().impir_last_error().decode(errors="replace")
+
+
+def impir_device_sm_count() -> int:
+    return int(lib().impir_device_sm_count())
+
+
+def impir_timing_enable(enable: bool = True) -> None:
+    _check(lib().impir_timing_enable(1 if enable else 0), "impir_timing_enable")
+
+
+def impir_timing_read() -> tuple[float, int, int]:
+    """(summed fused-kernel ms, fused launches, all library launches) since the last enable."""
+    ms, nf, na = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().impir_timing_read(ctypes.byref(ms), ctypes.byref(nf), ctypes.byref(na)), "impir_timing_read")
+    return ms.value, nf.value, na.value
+
+
+# ---- small conveniences over the ABI (argument packing only) ----
+
+def pack_keys(keys: list[bytes]) -> tuple[bytes, np.ndarray]:
+    """Concatenates wire keys; returns (blob, uint32 byte offsets)."""
+    offs = np.zeros(len(keys), np.uint32)
+    o = 0
+    for i, k in enumerate(keys):
+        offs[i] = o
+        o += len(k)
+    return b"".join(keys), offs

@@ -1,0 +1,476 @@
+// fused.cuh — the fused full-domain DPF evaluation + dpXOR kernel for sm_103a.
+//
+// What one launch computes (§2.3, §3.2, §3.3, Algorithm 1): for every query q of a batch,
+//     acc[q] = XOR over j < min(N, 2^m_q) of lsb(R(m_q, j)) * D[j]
+// where R is the GGM tree of Eqs. (1)-(3) with AES-128 as the PRF.
+//
+// How (GB300 mapping of the paper's subtree split and two-stage reduction):
+//   * Work unit = (warp tile, query group). A warp tile is 32 * 2^s consecutive leaves: lane l
+//     owns the perfect subtree of 2^s leaves rooted at depth m - s (the paper's worker
+//     subtrees, §3.2). A query group is up to QC queries of one domain size (§3.4 batching).
+//   * Each lane walks root -> its subtree root (the branch-parallel walk, one AES per level),
+//     then expands its subtree depth-first, two children per AES key schedule, and writes
+//     the 2^s selection bits of its leaves into shared memory. Selection bits never touch HBM.
+//   * The warp then reads the tile's records once (coalesced 16-byte loads) and XORs each
+//     record into the QC per-query accumulators held in registers (TaskletXOR), folds lanes
+//     with warp shuffles (MasterXOR), and XORs the result into the per-query answer in global
+//     memory with 64-bit atomic XOR (AggregateSubresults; XOR is order-independent, so the
+//     result is bit-exact whatever the order).
+//   * A persistent grid: warps take work units from a global counter, units ordered tile-major
+//     so that concurrently running warps read the same DB tile (served from L2).
+//
+// AES: 32-bit T-tables (Te0..Te3) replicated per lane in shared memory. Row x of a 64 KiB
+// region holds [Te_a[x] for lanes 0..31 | Te_b[x] for lanes 0..31] (256 bytes), so the byte
+// offset of lane L's copy of Te[x] is x*256 + L*4 (+128 for the second table of the region):
+// one PRMT builds it from the state word, and the 32 lanes of a warp always hit 32 distinct
+// banks. Region A holds Te0|Te1, region B Te2|Te3 (128 KiB). S-box values are read from the
+// byte of a T-table entry that equals S[x] (Te2 byte 0, Te3 byte 1, Te0 byte 2, Te1 byte 3).
+#pragma once
+
+#include <cstdint>
+
+#include "impir_internal.h"
+
+namespace impir {
+
+extern __shared__ __align__(16) uint8_t g_smem[];
+
+struct Blk {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ Blk bxor(const Blk a, const Blk b) { return {a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w}; }
+
+// Byte offset of lane L's copy of Te[byte b of w]: (byte << 8) | lane4.
+__device__ __forceinline__ uint32_t tix(uint32_t w, uint32_t lane4, int b) {
+    return __byte_perm(w, lane4, 0x5504u | (uint32_t(b) << 4));
+}
+
+template <int K>
+__device__ __forceinline__ uint32_t T(uint32_t off) {
+    return *reinterpret_cast<const uint32_t*>(g_smem + off + (K & 1) * 128 + (K >> 1) * 65536);
+}
+
+// One full round: SubBytes, ShiftRows, MixColumns, AddRoundKey (FIPS-197 §5.1).
+__device__ __forceinline__ Blk aes_round(const Blk s, uint32_t L, uint32_t k0, uint32_t k1, uint32_t k2,
+                                         uint32_t k3) {
+    Blk o;
+    o.x = T<0>(tix(s.x, L, 0)) ^ T<1>(tix(s.y, L, 1)) ^ T<2>(tix(s.z, L, 2)) ^ T<3>(tix(s.w, L, 3)) ^ k0;
+    o.y = T<0>(tix(s.y, L, 0)) ^ T<1>(tix(s.z, L, 1)) ^ T<2>(tix(s.w, L, 2)) ^ T<3>(tix(s.x, L, 3)) ^ k1;
+    o.z = T<0>(tix(s.z, L, 0)) ^ T<1>(tix(s.w, L, 1)) ^ T<2>(tix(s.x, L, 2)) ^ T<3>(tix(s.y, L, 3)) ^ k2;
+    o.w = T<0>(tix(s.w, L, 0)) ^ T<1>(tix(s.x, L, 1)) ^ T<2>(tix(s.y, L, 2)) ^ T<3>(tix(s.z, L, 3)) ^ k3;
+    return o;
+}
+
+// Final round: SubBytes, ShiftRows, AddRoundKey.
+__device__ __forceinline__ Blk aes_final(const Blk s, uint32_t L, uint32_t k0, uint32_t k1, uint32_t k2,
+                                         uint32_t k3) {
+    Blk o;
+    o.x = (T<2>(tix(s.x, L, 0)) & 0xffu) ^ (T<3>(tix(s.y, L, 1)) & 0xff00u) ^ (T<0>(tix(s.z, L, 2)) & 0xff0000u) ^
+          (T<1>(tix(s.w, L, 3)) & 0xff000000u) ^ k0;
+    o.y = (T<2>(tix(s.y, L, 0)) & 0xffu) ^ (T<3>(tix(s.z, L, 1)) & 0xff00u) ^ (T<0>(tix(s.w, L, 2)) & 0xff0000u) ^
+          (T<1>(tix(s.x, L, 3)) & 0xff000000u) ^ k1;
+    o.z = (T<2>(tix(s.z, L, 0)) & 0xffu) ^ (T<3>(tix(s.w, L, 1)) & 0xff00u) ^ (T<0>(tix(s.x, L, 2)) & 0xff0000u) ^
+          (T<1>(tix(s.y, L, 3)) & 0xff000000u) ^ k2;
+    o.w = (T<2>(tix(s.w, L, 0)) & 0xffu) ^ (T<3>(tix(s.x, L, 1)) & 0xff00u) ^ (T<0>(tix(s.y, L, 2)) & 0xff0000u) ^
+          (T<1>(tix(s.z, L, 3)) & 0xff000000u) ^ k3;
+    return o;
+}
+
+// Column 0 of a full round (the only column the leaf bit depends on after round 8).
+__device__ __forceinline__ uint32_t aes_round_col0(const Blk s, uint32_t L, uint32_t k0) {
+    return T<0>(tix(s.x, L, 0)) ^ T<1>(tix(s.y, L, 1)) ^ T<2>(tix(s.z, L, 2)) ^ T<3>(tix(s.w, L, 3)) ^ k0;
+}
+
+// SubWord(RotWord(w)) of the key schedule (FIPS-197 §5.2) on a little-endian word.
+__device__ __forceinline__ uint32_t sub_rot(uint32_t w, uint32_t L) {
+    return (T<2>(tix(w, L, 1)) & 0xffu) ^ (T<3>(tix(w, L, 2)) & 0xff00u) ^ (T<0>(tix(w, L, 3)) & 0xff0000u) ^
+           (T<1>(tix(w, L, 0)) & 0xff000000u);
+}
+
+// lsb of S[byte 0 of v].
+__device__ __forceinline__ uint32_t sbox0_lsb(uint32_t v, uint32_t L) { return T<2>(tix(v, L, 0)) & 1u; }
+
+__device__ __forceinline__ constexpr uint32_t rcon(int r) {
+    return r == 1 ? 0x01u : r == 2 ? 0x02u : r == 3 ? 0x04u : r == 4 ? 0x08u : r == 5 ? 0x10u
+         : r == 6 ? 0x20u : r == 7 ? 0x40u : r == 8 ? 0x80u : r == 9 ? 0x1bu : 0x36u;
+}
+
+struct Key4 {
+    uint32_t a, b, c, d;
+};
+
+__device__ __forceinline__ void ks_next(Key4& k, uint32_t rc, uint32_t L) {
+    k.a ^= sub_rot(k.d, L) ^ rc;
+    k.b ^= k.a;
+    k.c ^= k.b;
+    k.d ^= k.c;
+}
+
+// ---- keyed PRF: PRF_p(x) = AES-128 with key p over enc(x) = (x, 0, ..., 0) ----
+
+// Round 1 of both encryptions. State after round 0 is p (x = 0) or p ^ 1 (x = 1): they
+// differ only in byte 0 of column 0, which only output column 0 of round 1 reads.
+__device__ __forceinline__ void keyed_round1(const Blk p, uint32_t L, const Key4& k, Blk& a, Blk& b) {
+    const uint32_t c0 = T<1>(tix(p.y, L, 1)) ^ T<2>(tix(p.z, L, 2)) ^ T<3>(tix(p.w, L, 3)) ^ k.a;
+    a.x = c0 ^ T<0>(tix(p.x, L, 0));
+    b.x = c0 ^ T<0>(tix(p.x ^ 1u, L, 0));
+    a.y = T<0>(tix(p.y, L, 0)) ^ T<1>(tix(p.z, L, 1)) ^ T<2>(tix(p.w, L, 2)) ^ T<3>(tix(p.x, L, 3)) ^ k.b;
+    a.z = T<0>(tix(p.z, L, 0)) ^ T<1>(tix(p.w, L, 1)) ^ T<2>(tix(p.x, L, 2)) ^ T<3>(tix(p.y, L, 3)) ^ k.c;
+    a.w = T<0>(tix(p.w, L, 0)) ^ T<1>(tix(p.x, L, 1)) ^ T<2>(tix(p.y, L, 2)) ^ T<3>(tix(p.z, L, 3)) ^ k.d;
+    b.y = a.y;
+    b.z = a.z;
+    b.w = a.w;
+}
+
+// Both children's PRF outputs (128-bit each) of parent seed p.
+__device__ __forceinline__ void keyed_pair(const Blk p, uint32_t L, Blk& a, Blk& b) {
+    Key4 k{p.x, p.y, p.z, p.w};
+    ks_next(k, rcon(1), L);
+    keyed_round1(p, L, k, a, b);
+#pragma unroll
+    for (int r = 2; r <= 9; ++r) {
+        ks_next(k, rcon(r), L);
+        a = aes_round(a, L, k.a, k.b, k.c, k.d);
+        b = aes_round(b, L, k.a, k.b, k.c, k.d);
+    }
+    ks_next(k, rcon(10), L);
+    a = aes_final(a, L, k.a, k.b, k.c, k.d);
+    b = aes_final(b, L, k.a, k.b, k.c, k.d);
+}
+
+// lsb of both PRF outputs: rounds 1-8 in full, then only what byte 0 of the output needs:
+// column 0 of round 9 and byte 0 of round 10 (whose round-key byte 0 is
+// rk9.w0.b0 ^ S[rk9.w3.b1] ^ 0x36).
+__device__ __forceinline__ uint32_t keyed_leaf_bits(const Blk p, uint32_t L) {
+    Key4 k{p.x, p.y, p.z, p.w};
+    Blk a, b;
+    ks_next(k, rcon(1), L);
+    keyed_round1(p, L, k, a, b);
+#pragma unroll
+    for (int r = 2; r <= 8; ++r) {
+        ks_next(k, rcon(r), L);
+        a = aes_round(a, L, k.a, k.b, k.c, k.d);
+        b = aes_round(b, L, k.a, k.b, k.c, k.d);
+    }
+    ks_next(k, rcon(9), L);
+    const uint32_t a9 = aes_round_col0(a, L, k.a);
+    const uint32_t b9 = aes_round_col0(b, L, k.a);
+    const uint32_t kbit = (k.a ^ sbox0_lsb(k.d >> 8, L)) & 1u;  // lsb(0x36) = 0
+    return ((sbox0_lsb(a9, L) ^ kbit) & 1u) | (((sbox0_lsb(b9, L) ^ kbit) & 1u) << 1);
+}
+
+// One child's PRF output (the root-to-subtree walk): x may differ between lanes.
+__device__ __forceinline__ Blk keyed_one(const Blk p, uint32_t x, uint32_t L) {
+    Key4 k{p.x, p.y, p.z, p.w};
+    Blk s{p.x ^ x, p.y, p.z, p.w};
+#pragma unroll
+    for (int r = 1; r <= 9; ++r) {
+        ks_next(k, rcon(r), L);
+        s = aes_round(s, L, k.a, k.b, k.c, k.d);
+    }
+    ks_next(k, rcon(10), L);
+    return aes_final(s, L, k.a, k.b, k.c, k.d);
+}
+
+// ---- MMO PRF: PRF_p(x) = AES_{K_x}(p) ^ p with fixed round keys rk[x][44] ----
+
+__device__ __forceinline__ void mmo_pair(const Blk p, uint32_t L, const uint32_t (&rk)[2][44], Blk& a, Blk& b) {
+    a = {p.x ^ rk[0][0], p.y ^ rk[0][1], p.z ^ rk[0][2], p.w ^ rk[0][3]};
+    b = {p.x ^ rk[1][0], p.y ^ rk[1][1], p.z ^ rk[1][2], p.w ^ rk[1][3]};
+#pragma unroll
+    for (int r = 1; r <= 9; ++r) {
+        a = aes_round(a, L, rk[0][4 * r], rk[0][4 * r + 1], rk[0][4 * r + 2], rk[0][4 * r + 3]);
+        b = aes_round(b, L, rk[1][4 * r], rk[1][4 * r + 1], rk[1][4 * r + 2], rk[1][4 * r + 3]);
+    }
+    a = bxor(aes_final(a, L, rk[0][40], rk[0][41], rk[0][42], rk[0][43]), p);
+    b = bxor(aes_final(b, L, rk[1][40], rk[1][41], rk[1][42], rk[1][43]), p);
+}
+
+__device__ __forceinline__ uint32_t mmo_leaf_bits(const Blk p, uint32_t L, const uint32_t (&rk)[2][44]) {
+    Blk a = {p.x ^ rk[0][0], p.y ^ rk[0][1], p.z ^ rk[0][2], p.w ^ rk[0][3]};
+    Blk b = {p.x ^ rk[1][0], p.y ^ rk[1][1], p.z ^ rk[1][2], p.w ^ rk[1][3]};
+#pragma unroll
+    for (int r = 1; r <= 8; ++r) {
+        a = aes_round(a, L, rk[0][4 * r], rk[0][4 * r + 1], rk[0][4 * r + 2], rk[0][4 * r + 3]);
+        b = aes_round(b, L, rk[1][4 * r], rk[1][4 * r + 1], rk[1][4 * r + 2], rk[1][4 * r + 3]);
+    }
+    const uint32_t a9 = aes_round_col0(a, L, rk[0][36]);
+    const uint32_t b9 = aes_round_col0(b, L, rk[1][36]);
+    const uint32_t ba = (sbox0_lsb(a9, L) ^ rk[0][40] ^ p.x) & 1u;
+    const uint32_t bb = (sbox0_lsb(b9, L) ^ rk[1][40] ^ p.x) & 1u;
+    return ba | (bb << 1);
+}
+
+__device__ __forceinline__ Blk mmo_one(const Blk p, uint32_t x, uint32_t L, const uint32_t (&rk)[2][44]) {
+    Blk s = {p.x ^ (x ? rk[1][0] : rk[0][0]), p.y ^ (x ? rk[1][1] : rk[0][1]), p.z ^ (x ? rk[1][2] : rk[0][2]),
+             p.w ^ (x ? rk[1][3] : rk[0][3])};
+#pragma unroll
+    for (int r = 1; r <= 9; ++r)
+        s = aes_round(s, L, x ? rk[1][4 * r] : rk[0][4 * r], x ? rk[1][4 * r + 1] : rk[0][4 * r + 1],
+                      x ? rk[1][4 * r + 2] : rk[0][4 * r + 2], x ? rk[1][4 * r + 3] : rk[0][4 * r + 3]);
+    s = aes_final(s, L, x ? rk[1][40] : rk[0][40], x ? rk[1][41] : rk[0][41], x ? rk[1][42] : rk[0][42],
+                  x ? rk[1][43] : rk[0][43]);
+    return bxor(s, p);
+}
+
+// ---- codewords C_t[x][d] of a wire key (8-byte aligned entries) ----
+
+__device__ __forceinline__ size_t cw_off(uint32_t m, uint32_t t, uint32_t x, uint32_t d) {
+    return 8 + size_t(t) * 32 * (m + 1) + (size_t(x) * (m + 1) + d) * 16;
+}
+
+__device__ __forceinline__ Blk cw_load(const uint8_t* kq, uint32_t m, uint32_t t, uint32_t x, uint32_t d) {
+    const uint2* p = reinterpret_cast<const uint2*>(kq + cw_off(m, t, x, d));
+    const uint2 lo = __ldg(p), hi = __ldg(p + 1);
+    return {lo.x, lo.y, hi.x, hi.y};
+}
+
+__device__ __forceinline__ uint32_t cw_lsb(const uint8_t* kq, uint32_t m, uint32_t t, uint32_t x, uint32_t d) {
+    return __ldg(kq + cw_off(m, t, x, d)) & 1u;
+}
+
+// Selection bits of lane's subtree: root -> depth D walk (Eq. (3) one edge per level), then
+// a depth-first expansion down to the leaves at depth m; bit r of `bits` (relative to the
+// warp tile) is lsb(R(m, tile_first_leaf + r)).
+template <int PRF>
+__device__ __forceinline__ void lane_eval(const FusedParams& P, const uint8_t* kq, uint32_t m, uint32_t D,
+                                          uint64_t sub, uint32_t sq, uint32_t* bits, uint32_t lane, uint32_t L) {
+    Blk node = cw_load(kq, m, 0, 0, 0);  // R(0,0) = C_0[0][0], Eq. (2)
+    for (uint32_t d = 1; d <= D; ++d) {
+        const uint32_t x = uint32_t(sub >> (D - d)) & 1u;
+        const uint32_t t = node.x & 1u;
+        const Blk c = cw_load(kq, m, t, x, d);
+        const Blk f = PRF == 0 ? keyed_one(node, x, L) : mmo_one(node, x, L, P.mmo_rk);
+        node = bxor(f, c);
+    }
+    if (sq == 0) {
+        atomicOr(&bits[lane >> 5], (node.x & 1u) << (lane & 31));
+        return;
+    }
+    Blk stk[kMaxLaneBits];
+    uint32_t depth = D, p = 0, acc = 0;
+    const uint32_t npairs = 1u << (sq - 1);
+    for (;;) {
+        const uint32_t t = node.x & 1u;
+        if (depth == m - 1) {
+            uint32_t b2 = PRF == 0 ? keyed_leaf_bits(node, L) : mmo_leaf_bits(node, L, P.mmo_rk);
+            b2 ^= cw_lsb(kq, m, t, 0, m) | (cw_lsb(kq, m, t, 1, m) << 1);
+            acc |= b2 << ((2 * p) & 31);
+            ++p;
+            if (sq >= 5 && (p & 15) == 0) {
+                bits[(lane << (sq - 5)) + ((p - 1) >> 4)] = acc;
+                acc = 0;
+            }
+            if (p == npairs) break;
+            depth = m - 1 - (__ffs(int(p)) - 1);
+            node = stk[depth - D];
+        } else {
+            const Blk c0 = cw_load(kq, m, t, 0, depth + 1);
+            const Blk c1 = cw_load(kq, m, t, 1, depth + 1);
+            Blk a, b;
+            if (PRF == 0)
+                keyed_pair(node, L, a, b);
+            else
+                mmo_pair(node, L, P.mmo_rk, a, b);
+            ++depth;
+            stk[depth - D] = bxor(b, c1);
+            node = bxor(a, c0);
+        }
+    }
+    if (sq < 5) atomicOr(&bits[(lane << sq) >> 5], acc << ((lane << sq) & 31));
+}
+
+__device__ __forceinline__ uint4 ld_db(const uint4* p) { return __ldg(p); }
+
+__device__ __forceinline__ void red_xor(uint4* dst, const uint4 v) {
+    if (v.x | v.y)
+        atomicXor(reinterpret_cast<unsigned long long*>(dst),
+                  (unsigned long long)v.x | ((unsigned long long)v.y << 32));
+    if (v.z | v.w)
+        atomicXor(reinterpret_cast<unsigned long long*>(dst) + 1,
+                  (unsigned long long)v.z | ((unsigned long long)v.w << 32));
+}
+
+__device__ __forceinline__ void xor_masked(uint4& a, const uint4 v, uint32_t msk) {
+    a.x ^= v.x & msk;
+    a.y ^= v.y & msk;
+    a.z ^= v.z & msk;
+    a.w ^= v.w & msk;
+}
+
+__device__ __forceinline__ uint4 bxor4(const uint4 a, const uint4 b) {
+    return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
+}
+
+__device__ __forceinline__ uint4 shfl_xor4(const uint4 v, int off) {
+    return make_uint4(__shfl_xor_sync(0xffffffffu, v.x, off), __shfl_xor_sync(0xffffffffu, v.y, off),
+                      __shfl_xor_sync(0xffffffffu, v.z, off), __shfl_xor_sync(0xffffffffu, v.w, off));
+}
+
+// dpXOR of one warp tile for the group's queries: records [tile_base, tile_base + nrec).
+template <int QC, int NK>
+__device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_base, uint32_t nrec,
+                                          const uint32_t* bits, uint32_t count, const uint32_t* qidx, uint4* acc_out,
+                                          uint32_t lane) {
+    const uint32_t W = P.words;
+    const uint32_t bw = P.bits_words;
+    if constexpr (NK == 1) {
+        // W <= 32: R records per step, lane -> (record lr, word lk)
+        const uint32_t R = 32u / W, lr = lane / W, lk = lane - lr * W;
+        const bool on = lr < R;
+        uint4 acc[QC];
+#pragma unroll
+        for (int q = 0; q < QC; ++q) acc[q] = make_uint4(0, 0, 0, 0);
+        const uint4* base = P.db + tile_base * W + lk;
+        constexpr int U = 4;
+        for (uint32_t r0 = 0; r0 < nrec; r0 += U * R) {
+            uint4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t r = r0 + u * R + lr;
+                v[u] = (on && r < nrec) ? ld_db(base + size_t(r) * W) : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t r = min(r0 + u * R + lr, nrec - 1);
+#pragma unroll
+                for (int q = 0; q < QC; ++q) {
+                    const uint32_t msk = 0u - ((bits[q * bw + (r >> 5)] >> (r & 31)) & 1u);
+                    xor_masked(acc[q], v[u], msk);
+                }
+            }
+        }
+        if (R * W == 32) {
+            for (uint32_t off = W; off < 32; off <<= 1)
+#pragma unroll
+                for (int q = 0; q < QC; ++q) acc[q] = bxor4(acc[q], shfl_xor4(acc[q], int(off)));
+            if (lr == 0)
+#pragma unroll
+                for (int q = 0; q < QC; ++q)
+                    if (uint32_t(q) < count) red_xor(acc_out + size_t(qidx[q]) * W + lk, acc[q]);
+        } else if (on) {
+#pragma unroll
+            for (int q = 0; q < QC; ++q)
+                if (uint32_t(q) < count) red_xor(acc_out + size_t(qidx[q]) * W + lk, acc[q]);
+        }
+    } else {
+        // W > 32: the whole warp reads one record per step, NK words per lane, in column passes
+        for (uint32_t c0 = 0; c0 < W; c0 += 32 * NK) {
+            uint4 acc[QC][NK];
+#pragma unroll
+            for (int q = 0; q < QC; ++q)
+#pragma unroll
+                for (int c = 0; c < NK; ++c) acc[q][c] = make_uint4(0, 0, 0, 0);
+            for (uint32_t r = 0; r < nrec; ++r) {
+                uint4 v[NK];
+                const uint4* rec = P.db + (tile_base + r) * W;
+#pragma unroll
+                for (int c = 0; c < NK; ++c) {
+                    const uint32_t k = c0 + lane + 32 * c;
+                    v[c] = k < W ? ld_db(rec + k) : make_uint4(0, 0, 0, 0);
+                }
+#pragma unroll
+                for (int q = 0; q < QC; ++q) {
+                    const uint32_t msk = 0u - ((bits[q * bw + (r >> 5)] >> (r & 31)) & 1u);
+#pragma unroll
+                    for (int c = 0; c < NK; ++c) xor_masked(acc[q][c], v[c], msk);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < QC; ++q)
+                if (uint32_t(q) < count)
+#pragma unroll
+                    for (int c = 0; c < NK; ++c) {
+                        const uint32_t k = c0 + lane + 32 * c;
+                        if (k < W) red_xor(acc_out + size_t(qidx[q]) * W + k, acc[q][c]);
+                    }
+        }
+    }
+}
+
+template <int QC, int NK>
+__global__ void __launch_bounds__(512, 1) fused_kernel(const __grid_constant__ FusedParams P) {
+    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+    const uint32_t lane = tid & 31, warp = tid >> 5;
+
+    // Replicated T-tables (see the layout note at the top of this file).
+    for (uint32_t i = tid; i < 256 * 32; i += nthr) {
+        const uint32_t x = i >> 5, l = i & 31;
+        const uint32_t t0 = __ldg(P.te0 + x);
+        uint32_t* ra = reinterpret_cast<uint32_t*>(g_smem + x * 256);
+        uint32_t* rb = reinterpret_cast<uint32_t*>(g_smem + 65536 + x * 256);
+        ra[l] = t0;
+        ra[32 + l] = __funnelshift_l(t0, t0, 8);
+        rb[l] = __funnelshift_l(t0, t0, 16);
+        rb[32 + l] = __funnelshift_l(t0, t0, 24);
+    }
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(P.ws);
+    SegDesc* segs = reinterpret_cast<SegDesc*>(g_smem + kTableBytes);
+    const uint32_t n_segs = hdr->n_segs;
+    const SegDesc* gsegs = reinterpret_cast<const SegDesc*>(P.ws + P.lay.off_segs);
+    for (uint32_t i = tid; i < n_segs; i += nthr) segs[i] = gsegs[i];
+    __syncthreads();
+
+    const unsigned long long n_units = hdr->n_units;
+    const uint32_t* perm = reinterpret_cast<const uint32_t*>(P.ws + P.lay.off_perm);
+    const GroupDesc* groups = reinterpret_cast<const GroupDesc*>(P.ws + P.lay.off_groups);
+    uint4* acc_out = reinterpret_cast<uint4*>(P.ws + P.lay.off_acc);
+    uint32_t* bits = reinterpret_cast<uint32_t*>(g_smem + kTableBytes + kSegSmemBytes) + warp * QC * P.bits_words;
+    const uint32_t L = lane * 4;
+
+    for (;;) {
+        unsigned long long u = 0;
+        if (lane == 0) u = atomicAdd(&hdr->counter, 1ull);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= n_units) break;
+        uint32_t j = 0;
+        while (j + 1 < n_segs && segs[j + 1].unit_lo <= u) ++j;
+        const unsigned long long off = u - segs[j].unit_lo;
+        const unsigned long long tile = segs[j].tile_lo + off / segs[j].count;
+        const GroupDesc gd = groups[uint32_t(off % segs[j].count)];
+
+        const uint32_t m = gd.m;
+        const uint32_t sq = m >= 5 ? min(P.lane_bits, m - 5) : 0u;
+        const uint32_t D = m - sq;
+        const unsigned long long dom = 1ull << m;
+        const unsigned long long n_eff = P.n_records < dom ? P.n_records : dom;
+        const unsigned long long TT = m >= 5 ? (32ull << sq) : dom;
+        const unsigned long long tile_base = tile * TT;
+        const uint32_t nrec = uint32_t(min(TT, n_eff - tile_base));
+        const uint32_t lanes = m >= 5 ? 32u : (1u << m);
+        const unsigned long long sub = tile * 32 + lane;
+        const bool lane_on = lane < lanes && (sub << sq) < n_eff;
+        const uint32_t nwords = uint32_t((TT + 31) >> 5);
+
+        for (int q = 0; q < QC; ++q)
+            for (uint32_t w = lane; w < nwords; w += 32) bits[q * P.bits_words + w] = 0;
+        __syncwarp();
+        const uint32_t* qidx = perm + gd.first;
+        for (uint32_t qi = 0; qi < gd.count; ++qi) {
+            const uint8_t* kq = P.keys + P.key_off[qidx[qi]];
+            const uint32_t prf = kq[1];
+            if (lane_on) {
+                if (prf == 0)
+                    lane_eval<0>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L);
+                else
+                    lane_eval<1>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L);
+            }
+        }
+        __syncwarp();
+        scan_tile<QC, NK>(P, tile_base, nrec, bits, gd.count, qidx, acc_out, lane);
+        __syncwarp();
+    }
+}
+
+// Sets the dynamic shared memory limit once and launches one instantiation.
+template <int QC, int NK>
+cudaError_t launch_fused_t(dim3 grid, dim3 block, size_t smem, cudaStream_t s, const FusedParams& p) {
+    static const cudaError_t attr = cudaFuncSetAttribute(fused_kernel<QC, NK>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (attr != cudaSuccess) return attr;
+    fused_kernel<QC, NK><<<grid, block, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace impir

@@ -1,0 +1,16 @@
+// fused_q4.cu — instantiations of the fused EvalAll + dpXOR kernel for 4 queries per warp.
+#include "fused.cuh"
+
+namespace impir {
+
+cudaError_t launch_fused_q4(uint32_t nk, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const FusedParams& p) {
+    switch (nk) {
+        case 1: return launch_fused_t<4, 1>(grid, block, smem, s, p);
+        case 2: return launch_fused_t<4, 2>(grid, block, smem, s, p);
+        case 4: return launch_fused_t<4, 4>(grid, block, smem, s, p);
+
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace impir

@@ -1,0 +1,670 @@
+// impir_host.cpp — host runtime behind include/impir.h: database registry, key intake,
+// launch configuration and autotuning, the synchronous and asynchronous answer paths, and
+// the client-side key generator used by tests.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/impir.h"
+#include "impir_internal.h"
+
+using namespace impir;
+
+namespace {
+
+thread_local std::string g_err;
+
+impir_status fail(impir_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+impir_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(IMPIR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// ---- per-process device state (the current device at first use) ----
+struct DeviceState {
+    bool ok = false;
+    std::string err;
+    int device = -1;
+    int sms = 0;
+    uint32_t* d_te0 = nullptr;
+    uint32_t mmo_rk[2][44];
+};
+
+DeviceState& device_state() {
+    static DeviceState st;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaError_t e = cudaGetDevice(&st.device);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&st.sms, cudaDevAttrMultiProcessorCount, st.device);
+        uint32_t te0[256];
+        host_aes_te0(te0);
+        if (e == cudaSuccess) e = cudaMalloc(&st.d_te0, sizeof te0);
+        if (e == cudaSuccess) e = cudaMemcpy(st.d_te0, te0, sizeof te0, cudaMemcpyHostToDevice);
+        host_aes_expand(reinterpret_cast<const uint8_t*>(IMPIR_MMO_KEY0), st.mmo_rk[0]);
+        host_aes_expand(reinterpret_cast<const uint8_t*>(IMPIR_MMO_KEY1), st.mmo_rk[1]);
+        if (e != cudaSuccess) {
+            st.err = cudaGetErrorString(e);
+            return;
+        }
+        st.ok = true;
+    });
+    return st;
+}
+
+impir_status need_device(DeviceState** out) {
+    DeviceState& st = device_state();
+    if (!st.ok) return fail(IMPIR_ECUDA, "CUDA device unavailable: %s", st.err.c_str());
+    *out = &st;
+    return IMPIR_OK;
+}
+
+// ---- database registry ----
+struct Db {
+    const void* d = nullptr;
+    uint64_t n = 0;
+    uint32_t bytes = 0, stride = 0;
+    bool owned = false;
+    bool live = false;
+    bool cfg_set = false;
+    impir_config cfg{};
+};
+
+std::mutex g_db_mu;
+std::vector<Db> g_dbs;
+
+impir_status get_db(int32_t h, Db* out) {
+    std::lock_guard<std::mutex> lk(g_db_mu);
+    if (h < 1 || size_t(h) > g_dbs.size() || !g_dbs[h - 1].live) return fail(IMPIR_EINVAL, "unknown database handle %d", h);
+    *out = g_dbs[h - 1];
+    return IMPIR_OK;
+}
+
+int32_t add_db(const Db& d) {
+    std::lock_guard<std::mutex> lk(g_db_mu);
+    g_dbs.push_back(d);
+    g_dbs.back().live = true;
+    return int32_t(g_dbs.size());
+}
+
+// ---- configuration ----
+uint32_t nk_for(uint32_t words) {
+    if (words <= 32) return 1;
+    const uint32_t need = (words + 31) / 32;
+    return need <= 2 ? 2 : need <= 4 ? 4 : 8;
+}
+
+size_t smem_for(const impir_config& c) {
+    return kTableBytes + kSegSmemBytes + size_t(c.warps_per_cta) * c.queries_per_warp * (size_t(1) << c.lane_bits) * 4;
+}
+
+constexpr size_t kSmemMax = 227 * 1024;
+
+impir_status check_config(const impir_config& c, uint32_t words) {
+    if (c.lane_bits > kMaxLaneBits) return fail(IMPIR_EINVAL, "lane_bits %u > %u", c.lane_bits, kMaxLaneBits);
+    if (c.queries_per_warp != 1 && c.queries_per_warp != 2 && c.queries_per_warp != 4 && c.queries_per_warp != 8)
+        return fail(IMPIR_EINVAL, "queries_per_warp must be 1, 2, 4 or 8");
+    if (c.queries_per_warp * nk_for(words) > 16)
+        return fail(IMPIR_EINVAL, "queries_per_warp %u too large for %u-byte records", c.queries_per_warp, words * 16);
+    if (c.warps_per_cta < 4 || c.warps_per_cta > 16) return fail(IMPIR_EINVAL, "warps_per_cta must be 4..16");
+    if (c.queries_per_launch > 1) return fail(IMPIR_EINVAL, "queries_per_launch must be 0 or 1");
+    if (smem_for(c) > kSmemMax) return fail(IMPIR_EINVAL, "configuration needs %zu bytes of shared memory", smem_for(c));
+    return IMPIR_OK;
+}
+
+// Largest lane_bits that keeps enough warp tiles for every warp of the grid busy.
+impir_config default_config(uint64_t n_records, uint32_t words, uint32_t n_queries, int sms) {
+    impir_config c{};
+    c.warps_per_cta = 16;
+    c.queries_per_launch = 0;
+    uint32_t qpw = 8;
+    while (qpw > 1 && (qpw * nk_for(words) > 16 || qpw > n_queries)) qpw >>= 1;
+    c.queries_per_warp = qpw;
+    const double warps = double(sms) * c.warps_per_cta;
+    const double groups = std::ceil(double(n_queries) / qpw);
+    c.lane_bits = 0;
+    for (uint32_t s = kMaxLaneBits; s + 1 > 0; --s) {
+        impir_config t = c;
+        t.lane_bits = s;
+        if (smem_for(t) > kSmemMax) continue;
+        const double tiles = std::ceil(double(n_records) / double(32ull << s));
+        if (groups * tiles >= 3.0 * warps || s == 0) {
+            c.lane_bits = s;
+            break;
+        }
+    }
+    if (c.lane_bits > 8) c.lane_bits = 8;
+    return c;
+}
+
+impir_config config_for(const Db& db, uint32_t n_queries, int sms) {
+    if (db.cfg_set) return db.cfg;
+    return default_config(db.n, db.stride / 16, n_queries, sms);
+}
+
+// ---- key intake on the host (validation before any launch) ----
+impir_status parse_host_keys(const uint8_t* keys, uint32_t n, std::vector<uint32_t>& offs, size_t& total) {
+    offs.resize(n);
+    size_t o = 0;
+    for (uint32_t q = 0; q < n; ++q) {
+        const uint8_t* k = keys + o;
+        const uint32_t m = k[2];
+        if (k[0] != IMPIR_KEY_VERSION) return fail(IMPIR_EINVAL, "key %u: version %u", q, k[0]);
+        if (k[1] > 1) return fail(IMPIR_EINVAL, "key %u: unknown prf %u", q, k[1]);
+        if (m < 1 || m > IMPIR_MAX_DOMAIN_BITS) return fail(IMPIR_EINVAL, "key %u: domain bits %u", q, m);
+        for (int i = 3; i < 8; ++i)
+            if (k[i]) return fail(IMPIR_EINVAL, "key %u: reserved header byte %d is not zero", q, i);
+        const size_t z[3] = {8 + size_t(m + 1) * 16, 8 + size_t(m + 1) * 32, 8 + size_t(m + 1) * 48};
+        for (size_t zi : z)
+            for (int b = 0; b < 16; ++b)
+                if (k[zi + b]) return fail(IMPIR_EINVAL, "key %u: column-0 codeword other than the root is not zero", q);
+        if (o > 0xffffffffull) return fail(IMPIR_EINVAL, "keys exceed 4 GiB");
+        offs[q] = uint32_t(o);
+        o += impir_key_bytes(m);
+    }
+    total = o;
+    return IMPIR_OK;
+}
+
+// ---- kernel timing (events around fused launches) ----
+struct Timing {
+    std::mutex mu;
+    bool on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    double fused_ms = 0;
+    uint64_t fused = 0, all = 0;
+};
+Timing g_timing;
+
+bool timing_on() {
+    std::lock_guard<std::mutex> lk(g_timing.mu);
+    return g_timing.on;
+}
+
+void count_launches(uint64_t n) {
+    std::lock_guard<std::mutex> lk(g_timing.mu);
+    if (g_timing.on) g_timing.all += n;
+}
+
+// ---- launches ----
+impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_config& cfg, const uint8_t* d_keys,
+                          const uint32_t* d_off, uint32_t n, uint8_t* d_out, uint8_t* d_ws, cudaStream_t st) {
+    const WsLayout lay = ws_layout(n, db.stride);
+    SetupParams sp{};
+    sp.keys = d_keys;
+    sp.key_off = d_off;
+    sp.ws = d_ws;
+    sp.lay = lay;
+    sp.n_records = db.n;
+    sp.n_queries = n;
+    sp.words = db.stride / 16;
+    sp.lane_bits = cfg.lane_bits;
+    sp.qpw = cfg.queries_per_warp;
+    CK(launch_setup(sp, st), "setup kernel launch");
+
+    FusedParams fp{};
+    fp.db = static_cast<const uint4*>(db.d);
+    fp.keys = d_keys;
+    fp.key_off = d_off;
+    fp.ws = d_ws;
+    fp.te0 = dev.d_te0;
+    fp.lay = lay;
+    fp.n_records = db.n;
+    fp.n_queries = n;
+    fp.words = db.stride / 16;
+    fp.lane_bits = cfg.lane_bits;
+    fp.bits_words = 1u << cfg.lane_bits;
+    std::memcpy(fp.mmo_rk, dev.mmo_rk, sizeof fp.mmo_rk);
+    const size_t smem = smem_for(cfg);
+    const bool timed = timing_on();
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (timed) {
+        CK(cudaEventCreate(&ev0), "event create");
+        CK(cudaEventCreate(&ev1), "event create");
+        CK(cudaEventRecord(ev0, st), "event record");
+    }
+    CK(launch_fused(cfg.queries_per_warp, nk_for(fp.words), dim3(dev.sms), dim3(cfg.warps_per_cta * 32), smem, st, fp),
+       "fused kernel launch");
+    if (timed) {
+        CK(cudaEventRecord(ev1, st), "event record");
+        std::lock_guard<std::mutex> lk(g_timing.mu);
+        g_timing.pending.emplace_back(ev0, ev1);
+        g_timing.fused += 1;
+    }
+    count_launches(3);
+
+    FinalizeParams zp{};
+    zp.ws = d_ws;
+    zp.lay = lay;
+    zp.out = d_out;
+    zp.n_queries = n;
+    zp.record_bytes = db.bytes;
+    zp.stride = db.stride;
+    CK(launch_finalize(zp, st), "finalize kernel launch");
+    return IMPIR_OK;
+}
+
+impir_status answer_async_impl(const Db& db, const impir_config* cfg_in, const uint8_t* d_keys, const uint32_t* d_off,
+                               uint32_t n, uint8_t* d_out, void* d_ws, size_t ws_bytes, cudaStream_t st) {
+    DeviceState* dev;
+    if (impir_status s = need_device(&dev)) return s;
+    if (n == 0) return IMPIR_OK;
+    if (!d_keys || !d_off || !d_out || !d_ws) return fail(IMPIR_EINVAL, "NULL device buffer");
+    if (reinterpret_cast<uintptr_t>(d_ws) & 255) return fail(IMPIR_EINVAL, "workspace must be 256-byte aligned");
+    const impir_config cfg = cfg_in ? *cfg_in : config_for(db, n, dev->sms);
+    if (impir_status s = check_config(cfg, db.stride / 16)) return s;
+    if (cfg.queries_per_launch == 1) {
+        if (ws_bytes < ws_layout(1, db.stride).total) return fail(IMPIR_ENOMEM, "workspace too small");
+        for (uint32_t q = 0; q < n; ++q)
+            if (impir_status s = launch_batch(*dev, db, cfg, d_keys, d_off + q, 1, d_out + size_t(q) * db.bytes,
+                                              static_cast<uint8_t*>(d_ws), st))
+                return s;
+        return IMPIR_OK;
+    }
+    if (ws_bytes < ws_layout(n, db.stride).total)
+        return fail(IMPIR_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed", ws_bytes,
+                    ws_layout(n, db.stride).total);
+    return launch_batch(*dev, db, cfg, d_keys, d_off, n, d_out, static_cast<uint8_t*>(d_ws), st);
+}
+
+// ---- synchronous path context: cached device and pinned buffers ----
+struct SyncCtx {
+    std::mutex mu;
+    cudaStream_t stream = nullptr;
+    void *d_keys = nullptr, *d_off = nullptr, *d_ws = nullptr, *d_out = nullptr;
+    size_t c_keys = 0, c_off = 0, c_ws = 0, c_out = 0;
+    uint8_t* h_stage = nullptr;
+    size_t c_stage = 0;
+};
+
+SyncCtx g_sync;
+
+impir_status grow(void** p, size_t* cap, size_t need, bool pinned = false) {
+    if (*cap >= need) return IMPIR_OK;
+    size_t n = std::max(need, *cap * 2);
+    if (*p) {
+        if (pinned)
+            cudaFreeHost(*p);
+        else
+            cudaFree(*p);
+        *p = nullptr;
+        *cap = 0;
+    }
+    cudaError_t e = pinned ? cudaMallocHost(p, n) : cudaMalloc(p, n);
+    if (e != cudaSuccess) return fail(IMPIR_ENOMEM, "allocation of %zu bytes failed: %s", n, cudaGetErrorString(e));
+    *cap = n;
+    return IMPIR_OK;
+}
+
+// ---- tuning cache: (SMs, N, stride, batch, config hint) -> best configuration ----
+std::mutex g_tune_mu;
+std::map<std::tuple<int, uint64_t, uint32_t, uint32_t>, impir_config> g_tune;
+
+}  // namespace
+
+extern "C" {
+
+size_t impir_key_bytes(uint32_t m) { return 8 + size_t(64) * (m + 1); }
+
+const char* impir_last_error(void) { return g_err.c_str(); }
+
+impir_status impir_timing_enable(int enable) {
+    std::lock_guard<std::mutex> lk(g_timing.mu);
+    for (auto& p : g_timing.pending) {
+        cudaEventSynchronize(p.second);
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+    }
+    g_timing.pending.clear();
+    g_timing.on = enable != 0;
+    g_timing.fused_ms = 0;
+    g_timing.fused = g_timing.all = 0;
+    return IMPIR_OK;
+}
+
+impir_status impir_timing_read(double* fused_ms, uint64_t* fused_launches, uint64_t* all_launches) {
+    std::lock_guard<std::mutex> lk(g_timing.mu);
+    for (auto& p : g_timing.pending) {
+        CK(cudaEventSynchronize(p.second), "event sync");
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, p.first, p.second), "event time");
+        g_timing.fused_ms += ms;
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+    }
+    g_timing.pending.clear();
+    if (fused_ms) *fused_ms = g_timing.fused_ms;
+    if (fused_launches) *fused_launches = g_timing.fused;
+    if (all_launches) *all_launches = g_timing.all;
+    return IMPIR_OK;
+}
+
+int32_t impir_device_sm_count(void) {
+    DeviceState& st = device_state();
+    return st.ok ? st.sms : 0;
+}
+
+impir_status impir_db_load(const void* records, uint64_t n_records, uint32_t record_bytes, int32_t* db_handle) {
+    if (!records || !db_handle) return fail(IMPIR_EINVAL, "NULL argument");
+    if (n_records == 0 || record_bytes == 0) return fail(IMPIR_EINVAL, "empty database");
+    if (n_records > (1ull << IMPIR_MAX_DOMAIN_BITS)) return fail(IMPIR_EINVAL, "more than 2^40 records");
+    DeviceState* dev;
+    if (impir_status s = need_device(&dev)) return s;
+    const uint32_t stride = (record_bytes + 15u) & ~15u;
+    void* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, size_t(n_records) * stride);
+    if (e != cudaSuccess) return fail(IMPIR_ENOMEM, "device allocation of %llu bytes failed: %s",
+                                      (unsigned long long)(n_records * stride), cudaGetErrorString(e));
+    if (stride != record_bytes) {
+        e = cudaMemset(d, 0, size_t(n_records) * stride);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2D(d, stride, records, record_bytes, record_bytes, n_records, cudaMemcpyHostToDevice);
+    } else {
+        e = cudaMemcpy(d, records, size_t(n_records) * stride, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "database copy");
+    }
+    Db db;
+    db.d = d;
+    db.n = n_records;
+    db.bytes = record_bytes;
+    db.stride = stride;
+    db.owned = true;
+    *db_handle = add_db(db);
+    return IMPIR_OK;
+}
+
+impir_status impir_db_attach(const void* d_records, uint64_t n_records, uint32_t record_bytes, uint32_t stride_bytes,
+                             int32_t* db_handle) {
+    if (!d_records || !db_handle) return fail(IMPIR_EINVAL, "NULL argument");
+    if (n_records == 0 || record_bytes == 0) return fail(IMPIR_EINVAL, "empty database");
+    if (n_records > (1ull << IMPIR_MAX_DOMAIN_BITS)) return fail(IMPIR_EINVAL, "more than 2^40 records");
+    if (stride_bytes % 16 || stride_bytes < record_bytes) return fail(IMPIR_EINVAL, "bad stride %u", stride_bytes);
+    if (reinterpret_cast<uintptr_t>(d_records) & 15) return fail(IMPIR_EINVAL, "records must be 16-byte aligned");
+    Db db;
+    db.d = d_records;
+    db.n = n_records;
+    db.bytes = record_bytes;
+    db.stride = stride_bytes;
+    db.owned = false;
+    *db_handle = add_db(db);
+    return IMPIR_OK;
+}
+
+impir_status impir_db_free(int32_t h) {
+    Db db;
+    {
+        std::lock_guard<std::mutex> lk(g_db_mu);
+        if (h < 1 || size_t(h) > g_dbs.size() || !g_dbs[h - 1].live) return fail(IMPIR_EINVAL, "unknown database handle %d", h);
+        db = g_dbs[h - 1];
+        g_dbs[h - 1].live = false;
+    }
+    if (db.owned) cudaFree(const_cast<void*>(db.d));
+    return IMPIR_OK;
+}
+
+impir_status impir_db_info(int32_t h, uint64_t* n, uint32_t* bytes, uint32_t* stride, const void** d) {
+    Db db;
+    if (impir_status s = get_db(h, &db)) return s;
+    if (n) *n = db.n;
+    if (bytes) *bytes = db.bytes;
+    if (stride) *stride = db.stride;
+    if (d) *d = db.d;
+    return IMPIR_OK;
+}
+
+size_t impir_workspace_bytes(uint32_t n_queries, uint32_t stride_bytes) {
+    return ws_layout(n_queries, (stride_bytes + 15u) & ~15u).total;
+}
+
+impir_status impir_answer_async(int32_t h, const uint8_t* d_keys, const uint32_t* d_off, uint32_t n, uint8_t* d_out,
+                                void* d_ws, size_t ws_bytes, void* stream) {
+    Db db;
+    if (impir_status s = get_db(h, &db)) return s;
+    return answer_async_impl(db, nullptr, d_keys, d_off, n, d_out, d_ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+impir_status impir_workspace_status(const void* d_ws, uint32_t* n_bad, uint32_t* first_bad) {
+    if (!d_ws) return fail(IMPIR_EINVAL, "NULL workspace");
+    WsHeader h;
+    CK(cudaDeviceSynchronize(), "synchronize");
+    CK(cudaMemcpy(&h, d_ws, sizeof h, cudaMemcpyDeviceToHost), "workspace status copy");
+    if (n_bad) *n_bad = h.n_bad;
+    if (first_bad) *first_bad = h.first_bad;
+    return IMPIR_OK;
+}
+
+impir_status impir_answer(int32_t h, const uint8_t* keys, uint32_t n, uint8_t* out) {
+    Db db;
+    if (impir_status s = get_db(h, &db)) return s;
+    if (n == 0) return IMPIR_OK;
+    if (!keys || !out) return fail(IMPIR_EINVAL, "NULL argument");
+    DeviceState* dev;
+    if (impir_status s = need_device(&dev)) return s;
+    std::vector<uint32_t> offs;
+    size_t total = 0;
+    if (impir_status s = parse_host_keys(keys, n, offs, total)) return s;
+    std::lock_guard<std::mutex> lk(g_sync.mu);
+    if (!g_sync.stream) CK(cudaStreamCreateWithFlags(&g_sync.stream, cudaStreamNonBlocking), "stream create");
+    const impir_config cfg = config_for(db, n, dev->sms);
+    const size_t ws = cfg.queries_per_launch == 1 ? ws_layout(1, db.stride).total : ws_layout(n, db.stride).total;
+    const size_t out_bytes = size_t(n) * db.bytes;
+    const size_t stage = std::max(total + size_t(n) * 4, out_bytes);
+    if (impir_status s = grow(&g_sync.d_keys, &g_sync.c_keys, total)) return s;
+    if (impir_status s = grow(&g_sync.d_off, &g_sync.c_off, size_t(n) * 4)) return s;
+    if (impir_status s = grow(&g_sync.d_ws, &g_sync.c_ws, ws)) return s;
+    if (impir_status s = grow(&g_sync.d_out, &g_sync.c_out, out_bytes)) return s;
+    if (impir_status s = grow(reinterpret_cast<void**>(&g_sync.h_stage), &g_sync.c_stage, stage, true)) return s;
+    std::memcpy(g_sync.h_stage, keys, total);
+    std::memcpy(g_sync.h_stage + total, offs.data(), size_t(n) * 4);
+    cudaStream_t st = g_sync.stream;
+    CK(cudaMemcpyAsync(g_sync.d_keys, g_sync.h_stage, total, cudaMemcpyHostToDevice, st), "key upload");
+    CK(cudaMemcpyAsync(g_sync.d_off, g_sync.h_stage + total, size_t(n) * 4, cudaMemcpyHostToDevice, st), "offset upload");
+    if (impir_status s = answer_async_impl(db, &cfg, static_cast<const uint8_t*>(g_sync.d_keys),
+                                           static_cast<const uint32_t*>(g_sync.d_off), n,
+                                           static_cast<uint8_t*>(g_sync.d_out), g_sync.d_ws, g_sync.c_ws, st))
+        return s;
+    CK(cudaMemcpyAsync(g_sync.h_stage, g_sync.d_out, out_bytes, cudaMemcpyDeviceToHost, st), "answer download");
+    CK(cudaStreamSynchronize(st), "answer");
+    std::memcpy(out, g_sync.h_stage, out_bytes);
+    return IMPIR_OK;
+}
+
+impir_status impir_get_config(int32_t h, impir_config* cfg) {
+    if (!cfg) return fail(IMPIR_EINVAL, "NULL argument");
+    Db db;
+    if (impir_status s = get_db(h, &db)) return s;
+    DeviceState* dev;
+    if (impir_status s = need_device(&dev)) return s;
+    *cfg = config_for(db, 1, dev->sms);
+    return IMPIR_OK;
+}
+
+impir_status impir_set_config(int32_t h, const impir_config* cfg) {
+    if (!cfg) return fail(IMPIR_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(g_db_mu);
+    if (h < 1 || size_t(h) > g_dbs.size() || !g_dbs[h - 1].live) return fail(IMPIR_EINVAL, "unknown database handle %d", h);
+    if (impir_status s = check_config(*cfg, g_dbs[h - 1].stride / 16)) return s;
+    g_dbs[h - 1].cfg = *cfg;
+    g_dbs[h - 1].cfg_set = true;
+    return IMPIR_OK;
+}
+
+impir_status impir_autotune(int32_t h, const uint8_t* d_keys, const uint32_t* d_off, uint32_t n, uint8_t* d_out,
+                            void* d_ws, size_t ws_bytes, void* stream, impir_config* best) {
+    Db db;
+    if (impir_status s = get_db(h, &db)) return s;
+    DeviceState* dev;
+    if (impir_status s = need_device(&dev)) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const auto key = std::make_tuple(dev->sms, db.n, db.stride, n);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            if (best) *best = it->second;
+            return impir_set_config(h, &it->second);
+        }
+    }
+    const impir_config base = default_config(db.n, db.stride / 16, n, dev->sms);
+    std::vector<impir_config> cands;
+    for (uint32_t qpw : {1u, 2u, 4u, 8u}) {
+        if (qpw > 1 && qpw / 2 >= n) continue;
+        for (int ds = -3; ds <= 2; ++ds) {
+            const int s = int(base.lane_bits) + ds;
+            if (s < 0 || s > int(kMaxLaneBits)) continue;
+            impir_config c = base;
+            c.queries_per_warp = qpw;
+            c.lane_bits = uint32_t(s);
+            if (check_config(c, db.stride / 16) == IMPIR_OK) cands.push_back(c);
+        }
+    }
+    g_err.clear();
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    float best_ms = 1e30f;
+    impir_config best_c = base;
+    for (const impir_config& c : cands) {
+        if (impir_status s = answer_async_impl(db, &c, d_keys, d_off, n, d_out, d_ws, ws_bytes, st)) return s;
+        CK(cudaEventRecord(e0, st), "event record");
+        if (impir_status s = answer_async_impl(db, &c, d_keys, d_off, n, d_out, d_ws, ws_bytes, st)) return s;
+        CK(cudaEventRecord(e1, st), "event record");
+        CK(cudaEventSynchronize(e1), "event sync");
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1), "event time");
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = best_c;
+    }
+    if (best) *best = best_c;
+    return impir_set_config(h, &best_c);
+}
+
+// ---- client side ----
+
+impir_status impir_reconstruct(const uint8_t* r0, const uint8_t* r1, uint32_t record_bytes, uint8_t* out) {
+    if (!r0 || !r1 || !out) return fail(IMPIR_EINVAL, "NULL argument");
+    for (uint32_t b = 0; b < record_bytes; ++b) out[b] = r0[b] ^ r1[b];
+    return IMPIR_OK;
+}
+
+impir_status dpf_gen(uint64_t alpha, uint32_t m, impir_prf prf, const uint8_t rng_seed[32], uint8_t* key0,
+                     uint8_t* key1) {
+    if (!rng_seed || !key0 || !key1) return fail(IMPIR_EINVAL, "NULL argument");
+    if (m < 1 || m > IMPIR_MAX_DOMAIN_BITS) return fail(IMPIR_EINVAL, "domain bits %u outside 1..40", m);
+    if (prf != IMPIR_PRF_AES_KEYED && prf != IMPIR_PRF_AES_MMO) return fail(IMPIR_EINVAL, "unknown prf");
+    if (alpha >> m) return fail(IMPIR_EINVAL, "alpha >= 2^m");
+    uint64_t state = 0;
+    for (int w = 0; w < 4; ++w) {
+        uint64_t v = 0;
+        std::memcpy(&v, rng_seed + 8 * w, 8);  // little-endian hosts
+        state ^= v;
+    }
+    auto next64 = [&state]() {
+        uint64_t z = (state += 0x9e3779b97f4a7c15ull);
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        return z ^ (z >> 31);
+    };
+    auto draw = [&](uint8_t out[16]) {
+        uint64_t a = next64(), b = next64();
+        std::memcpy(out, &a, 8);
+        std::memcpy(out + 8, &b, 8);
+    };
+    uint32_t rk_mmo[2][44];
+    host_aes_expand(reinterpret_cast<const uint8_t*>(IMPIR_MMO_KEY0), rk_mmo[0]);
+    host_aes_expand(reinterpret_cast<const uint8_t*>(IMPIR_MMO_KEY1), rk_mmo[1]);
+    auto prf_eval = [&](const uint8_t s[16], int x, uint8_t out[16]) {
+        if (prf == IMPIR_PRF_AES_KEYED) {
+            uint32_t rk[44];
+            host_aes_expand(s, rk);
+            uint8_t blk[16] = {0};
+            blk[0] = uint8_t(x);
+            host_aes_encrypt(rk, blk, out);
+        } else {
+            host_aes_encrypt(rk_mmo[x], s, out);
+            for (int i = 0; i < 16; ++i) out[i] ^= s[i];
+        }
+    };
+    const size_t kb = impir_key_bytes(m);
+    std::memset(key0, 0, kb);
+    std::memset(key1, 0, kb);
+    for (uint8_t* k : {key0, key1}) {
+        k[0] = IMPIR_KEY_VERSION;
+        k[1] = uint8_t(prf);
+        k[2] = uint8_t(m);
+    }
+    auto cw = [m](uint8_t* k, int t, int x, uint32_t d) { return k + 8 + size_t(t) * 32 * (m + 1) + (size_t(x) * (m + 1) + d) * 16; };
+    uint8_t pa[16], pb[16];
+    draw(pa);
+    draw(pb);
+    pb[0] = uint8_t((pb[0] & 0xfe) | ((pa[0] & 1) ^ 1));
+    std::memcpy(cw(key0, 0, 0, 0), pa, 16);
+    std::memcpy(cw(key1, 0, 0, 0), pb, 16);
+    for (uint32_t d = 1; d <= m; ++d) {
+        const int a = pa[0] & 1;
+        const int on = int((alpha >> (m - d)) & 1);
+        uint8_t fa[2][16], fb[2][16];
+        for (int x = 0; x < 2; ++x) {
+            prf_eval(pa, x, fa[x]);
+            prf_eval(pb, x, fb[x]);
+            uint8_t r[16], delta[16] = {0};
+            draw(r);
+            if (x == on) {
+                if (d < m) {
+                    draw(delta);
+                    delta[0] |= 1;
+                } else {
+                    delta[0] = 1;
+                }
+            }
+            uint8_t* ca = cw(key0, a, x, d);
+            uint8_t* cb = cw(key0, 1 - a, x, d);
+            for (int i = 0; i < 16; ++i) {
+                ca[i] = r[i];
+                cb[i] = uint8_t(r[i] ^ fa[x][i] ^ fb[x][i] ^ delta[i]);
+            }
+        }
+        for (int t = 0; t < 2; ++t)
+            for (int x = 0; x < 2; ++x) std::memcpy(cw(key1, t, x, d), cw(key0, t, x, d), 16);
+        const uint8_t* ca = cw(key0, a, on, d);
+        const uint8_t* cb = cw(key0, 1 - a, on, d);
+        for (int i = 0; i < 16; ++i) {
+            pa[i] = fa[on][i] ^ ca[i];
+            pb[i] = fb[on][i] ^ cb[i];
+        }
+    }
+    return IMPIR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,162 @@
+// setup.cu — per-batch scheduling and answer write-out kernels.
+//
+// setup_kernel (one CTA) reads the key headers on the device, validates them, sorts the
+// queries by domain size (largest first), forms query groups of one domain size (the
+// paper's queries handled together, §3.4), and builds the tile-major work-unit schedule the
+// fused kernel walks: warp tile i is covered by every group whose DB prefix min(N, 2^m)
+// reaches it, so the schedule is a handful of segments (one per distinct domain size). It
+// also zeroes the per-query accumulators and the work counter.
+//
+// finalize_kernel copies each query's accumulator (record stride) into the caller's
+// answer buffer (record_bytes per query).
+#include "impir_internal.h"
+
+namespace impir {
+
+__global__ void __launch_bounds__(1024) setup_kernel(const SetupParams S) {
+    __shared__ uint32_t hist[kMaxDomainBits + 1], cursor[kMaxDomainBits + 1];
+    __shared__ uint32_t bstart[kMaxDomainBits + 1], gstart[kMaxDomainBits + 1], ngrp[kMaxDomainBits + 1];
+    __shared__ uint32_t s_nbad, s_first_bad, s_ngroups;
+    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(S.ws);
+    uint32_t* perm = reinterpret_cast<uint32_t*>(S.ws + S.lay.off_perm);
+    uint32_t* qm = reinterpret_cast<uint32_t*>(S.ws + S.lay.off_qm);
+    GroupDesc* groups = reinterpret_cast<GroupDesc*>(S.ws + S.lay.off_groups);
+    SegDesc* segs = reinterpret_cast<SegDesc*>(S.ws + S.lay.off_segs);
+    uint4* acc = reinterpret_cast<uint4*>(S.ws + S.lay.off_acc);
+
+    if (tid <= kMaxDomainBits) hist[tid] = cursor[tid] = 0;
+    if (tid == 0) {
+        s_nbad = 0;
+        s_first_bad = 0xffffffffu;
+    }
+    __syncthreads();
+
+    // 1. validate each key's header and column 0 (a1 key intake)
+    for (uint32_t q = tid; q < S.n_queries; q += nthr) {
+        const uint32_t off = S.key_off[q];
+        bool ok = (off & 7u) == 0;
+        uint32_t m = 0;
+        if (ok) {
+            const uint8_t* k = S.keys + off;
+            const uint2 h = *reinterpret_cast<const uint2*>(k);
+            const uint32_t ver = h.x & 0xffu, prf = (h.x >> 8) & 0xffu;
+            m = (h.x >> 16) & 0xffu;
+            ok = ver == 1 && prf <= 1 && m >= 1 && m <= kMaxDomainBits && (h.x >> 24) == 0 && h.y == 0;
+            if (ok) {
+                const size_t z[3] = {8 + size_t(m + 1) * 16, 8 + size_t(m + 1) * 32, 8 + size_t(m + 1) * 48};
+                for (int i = 0; i < 3; ++i) {
+                    const uint2* p = reinterpret_cast<const uint2*>(k + z[i]);
+                    const uint2 a = p[0], b = p[1];
+                    ok = ok && (a.x | a.y | b.x | b.y) == 0;
+                }
+            }
+        }
+        qm[q] = ok ? m : 0;
+        if (ok) {
+            atomicAdd(&hist[m], 1u);
+        } else {
+            atomicAdd(&s_nbad, 1u);
+            atomicMin(&s_first_bad, q);
+        }
+    }
+    __syncthreads();
+
+    // 2. buckets by domain size, largest first; groups of at most qpw queries per bucket;
+    //    tile-major segments (a tile is 32 << lane_bits leaves for m >= 5 + lane_bits,
+    //    otherwise the whole domain is one tile)
+    if (tid == 0) {
+        uint32_t pos = 0, g = 0;
+        for (int m = kMaxDomainBits; m >= 1; --m) {
+            bstart[m] = pos;
+            gstart[m] = g;
+            ngrp[m] = (hist[m] + S.qpw - 1) / S.qpw;
+            pos += hist[m];
+            g += ngrp[m];
+        }
+        s_ngroups = g;
+        const unsigned long long tbig = 32ull << S.lane_bits;
+        unsigned long long prev = 0, unit = 0;
+        uint32_t nseg = 0;
+        for (uint32_t m = 1; m <= kMaxDomainBits; ++m) {
+            if (hist[m] == 0) continue;
+            const unsigned long long dom = 1ull << m;
+            const unsigned long long n_eff = S.n_records < dom ? S.n_records : dom;
+            const unsigned long long tiles = m >= 5 + S.lane_bits ? (n_eff + tbig - 1) / tbig : 1ull;
+            if (tiles > prev) {
+                const uint32_t gcum = gstart[m] + ngrp[m];  // groups with domain bits >= m
+                segs[nseg].tile_lo = prev;
+                segs[nseg].unit_lo = unit;
+                segs[nseg].count = gcum;
+                segs[nseg].pad = 0;
+                segs[nseg].pad2 = 0;
+                unit += (tiles - prev) * gcum;
+                prev = tiles;
+                ++nseg;
+            }
+        }
+        hdr->counter = 0;
+        hdr->n_units = unit;
+        hdr->n_bad = s_nbad;
+        hdr->first_bad = s_first_bad;
+        hdr->n_groups = g;
+        hdr->n_segs = nseg;
+    }
+    __syncthreads();
+
+    // 3. scatter queries into their buckets (order inside a bucket does not matter: XOR
+    //    answers are independent of which queries share a group)
+    for (uint32_t q = tid; q < S.n_queries; q += nthr) {
+        const uint32_t m = qm[q];
+        if (m) perm[bstart[m] + atomicAdd(&cursor[m], 1u)] = q;
+    }
+    // 4. group descriptors
+    for (uint32_t gi = tid; gi < s_ngroups; gi += nthr) {
+        uint32_t m = kMaxDomainBits;
+        while (m > 1 && !(gi >= gstart[m] && gi < gstart[m] + ngrp[m])) --m;
+        const uint32_t k = gi - gstart[m];
+        GroupDesc d;
+        d.first = bstart[m] + k * S.qpw;
+        d.count = min(S.qpw, hist[m] - k * S.qpw);
+        d.m = m;
+        d.pad = 0;
+        groups[gi] = d;
+    }
+    // 5. zero the accumulators
+    const size_t nacc = size_t(S.n_queries) * S.words;
+    for (size_t i = tid; i < nacc; i += nthr) acc[i] = make_uint4(0, 0, 0, 0);
+}
+
+__global__ void finalize_kernel(const FinalizeParams F) {
+    const uint8_t* acc = F.ws + F.lay.off_acc;
+    const size_t n = size_t(F.n_queries) * F.record_bytes;
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+        const size_t q = i / F.record_bytes, b = i - q * F.record_bytes;
+        F.out[i] = acc[q * F.stride + b];
+    }
+}
+
+cudaError_t launch_setup(const SetupParams& p, cudaStream_t s) {
+    setup_kernel<<<1, 1024, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t s) {
+    const size_t n = size_t(p.n_queries) * p.record_bytes;
+    const unsigned blocks = unsigned(n / 256 + 1 < 1024 ? n / 256 + 1 : 1024);
+    finalize_kernel<<<blocks, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused(uint32_t qpw, uint32_t nk, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                         const FusedParams& p) {
+    switch (qpw) {
+        case 1: return launch_fused_q1(nk, grid, block, smem, s, p);
+        case 2: return launch_fused_q2(nk, grid, block, smem, s, p);
+        case 4: return launch_fused_q4(nk, grid, block, smem, s, p);
+        case 8: return launch_fused_q8(nk, grid, block, smem, s, p);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace impir
