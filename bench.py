@@ -173,7 +173,6 @@ def run_reference(args, world, rank):
     oracle.build()
     w = make_workload(args.workload)
     cores = os.cpu_count() or 1
-    b0 = w.batches[0]
     # one query per step, taken round-robin from the workload (records regenerated once)
     db = workloads.make_db(w.n_records, w.record_bytes, w.db_seed)
     qs = [(m, a, s) for b in w.batches for m, a, s in zip(b.ms, b.alphas, b.seeds)]
@@ -186,7 +185,6 @@ def run_reference(args, world, rank):
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
-    del b0
     total = sum(times)
     v = args.steps / total
     print(json.dumps({
@@ -258,7 +256,7 @@ def main():
         big = max(batches, key=lambda bt: bt["n"])
         tuned = impir.impir_autotune(dbh, big["d_keys0"], big["d_off"], big["n"], big["d_out"], big["d_ws"],
                                      big["wsb"], stream).as_dict()
-    cfg = impir.impir_get_config(dbh).as_dict()
+    cfg = impir.impir_get_config(dbh, max(bt["n"] for bt in batches)).as_dict()
 
     # parity on the GPU answers of this run: both servers, reconstruction of every query
     run_step(1)
@@ -313,7 +311,7 @@ def main():
     plain = None
     if not args.no_plain:
         impir.impir_set_config(dbh, cfg["lane_bits"], 1, cfg["warps_per_cta"], 1)
-        pc = impir.impir_get_config(dbh).as_dict()
+        pc = impir.impir_get_config(dbh, 1).as_dict()
         run_step()
         stream.synchronize()
         p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -345,11 +343,7 @@ def main():
         agree = True
         for bi, i in qs:
             bt = batches[bi]
-            key = bt["blob0"][:0]
-            k0, _ = impir.pack_keys([]) if False else (None, None)
-            o = 0
-            for j in range(i):
-                o += impir.impir_key_bytes(bt["ms"][j])
+            o = sum(impir.impir_key_bytes(m) for m in bt["ms"][:i])
             key = bt["blob0"][o:o + impir.impir_key_bytes(bt["ms"][i])]
             r = oracle.answer(key, db, N, B, threads=cores)
             agree &= r == ans0[bi][i].tobytes()

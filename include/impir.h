@@ -134,8 +134,10 @@ typedef struct {
     uint32_t queries_per_launch;
 } impir_config;
 
-/* Gets or sets the configuration used for a database (set validates it: EINVAL). */
-impir_status impir_get_config(int32_t db_handle, impir_config* cfg);
+/* Gets the configuration a batch of n_queries keys would be launched with on this database
+ * (the one set or tuned for it, else the built-in default for that batch size), or sets one
+ * for all later batches (set validates it: EINVAL). */
+impir_status impir_get_config(int32_t db_handle, uint32_t n_queries, impir_config* cfg);
 impir_status impir_set_config(int32_t db_handle, const impir_config* cfg);
 
 /* Times candidate configurations on the given asynchronous problem (same arguments as

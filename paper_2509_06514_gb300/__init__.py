@@ -76,7 +76,7 @@ def lib():
                                                       ctypes.c_size_t, vp]),
                 "impir_workspace_status": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_uint32),
                                                           ctypes.POINTER(ctypes.c_uint32)]),
-                "impir_get_config": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(impir_config)]),
+                "impir_get_config": (ctypes.c_int, [ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(impir_config)]),
                 "impir_set_config": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(impir_config)]),
                 "impir_autotune": (ctypes.c_int, [ctypes.c_int32, vp, vp, ctypes.c_uint32, vp, vp, ctypes.c_size_t,
                                                   vp, ctypes.POINTER(impir_config)]),
@@ -184,9 +184,9 @@ def impir_workspace_status(d_workspace) -> tuple[int, int]:
     return nb.value, fb.value
 
 
-def impir_get_config(db: int) -> impir_config:
+def impir_get_config(db: int, n_queries: int = 1) -> impir_config:
     c = impir_config()
-    _check(lib().impir_get_config(db, ctypes.byref(c)), "impir_get_config")
+    _check(lib().impir_get_config(db, n_queries, ctypes.byref(c)), "impir_get_config")
     return c
 
 

@@ -492,13 +492,13 @@ impir_status impir_answer(int32_t h, const uint8_t* keys, uint32_t n, uint8_t* o
     return IMPIR_OK;
 }
 
-impir_status impir_get_config(int32_t h, impir_config* cfg) {
+impir_status impir_get_config(int32_t h, uint32_t n_queries, impir_config* cfg) {
     if (!cfg) return fail(IMPIR_EINVAL, "NULL argument");
     Db db;
     if (impir_status s = get_db(h, &db)) return s;
     DeviceState* dev;
     if (impir_status s = need_device(&dev)) return s;
-    *cfg = config_for(db, 1, dev->sms);
+    *cfg = config_for(db, n_queries ? n_queries : 1, dev->sms);
     return IMPIR_OK;
 }
 

@@ -1,0 +1,149 @@
+"""GPU parity at the full workload sizes, in the launch configuration the benchmark uses:
+every query's two answers reconstruct its record (r_A ^ r_B = D[alpha]); sampled queries
+equal the CPU oracle's answer bit for bit; the batched form equals the one-query-per-launch
+form; an autotuned configuration and a captured CUDA graph give the same bits."""
+import numpy as np
+import pytest
+
+import paper_2509_06514_gb300 as impir
+from paper_2509_06514_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2509_06514_gb300 import build
+    build.build()
+    return torch
+
+
+class Loaded:
+    """A workload resident on the device with both servers' keys."""
+
+    def __init__(self, torch, w, prf=impir.IMPIR_PRF_AES_KEYED):
+        self.torch, self.w = torch, w
+        self.db = workloads.make_db(w.n_records, w.record_bytes, w.db_seed)
+        self.h = impir.impir_db_load(self.db, w.n_records, w.record_bytes)
+        self.stride = impir.impir_db_info(self.h)["stride_bytes"]
+        self.batches = []
+        for b in w.batches:
+            pairs = [impir.dpf_gen(a, m, prf, s) for m, a, s in zip(b.ms, b.alphas, b.seeds)]
+            self.batches.append((b, [p[0] for p in pairs], [p[1] for p in pairs]))
+
+    def answer_async(self, keys, stream=None):
+        torch = self.torch
+        blob, offs = impir.pack_keys(keys)
+        n = len(keys)
+        d_keys = torch.from_numpy(np.frombuffer(blob, np.uint8).copy()).cuda()
+        d_off = torch.from_numpy(offs.view(np.int32).copy()).cuda()
+        d_out = torch.zeros((n, self.w.record_bytes), dtype=torch.uint8, device="cuda")
+        wsb = impir.impir_workspace_bytes(n, self.stride)
+        d_ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+        impir.impir_answer_async(self.h, d_keys, d_off, n, d_out, d_ws, wsb, stream)
+        torch.cuda.synchronize()
+        return d_out.cpu().numpy()
+
+    def check_reconstruction(self, r0, r1, alphas):
+        for i, a in enumerate(alphas):
+            assert np.array_equal(r0[i] ^ r1[i], self.db[a]), i
+
+    def close(self):
+        impir.impir_db_free(self.h)
+
+
+def oracle_check(orc, L, keys, got, idx):
+    for i in idx:
+        want = orc.answer(keys[i], L.db, L.w.n_records, L.w.record_bytes, threads=16)
+        assert got[i].tobytes() == want, i
+
+
+def test_single_query_2mib(torch_cuda, orc):
+    """N=2^16 x 32 B, m=16, one query per launch, both servers, full oracle check."""
+    L = Loaded(torch_cuda, workloads.single_query())
+    try:
+        b, k0, k1 = L.batches[0]
+        impir.impir_set_config(L.h, 3, 1, 16, 1)
+        r0 = impir.impir_answer(L.h, k0[0], 1, 32)
+        r1 = impir.impir_answer(L.h, k1[0], 1, 32)
+        L.check_reconstruction(r0, r1, b.alphas)
+        oracle_check(orc, L, k0, r0, [0])
+        oracle_check(orc, L, k1, r1, [0])
+    finally:
+        L.close()
+
+
+def test_batched_256mib(torch_cuda, orc):
+    """N=2^20 x 256 B, 64 queries of domain 2^20 in one persistent launch."""
+    L = Loaded(torch_cuda, workloads.batched_256mib())
+    try:
+        b, k0, k1 = L.batches[0]
+        r0 = L.answer_async(k0)
+        r1 = L.answer_async(k1)
+        L.check_reconstruction(r0, r1, b.alphas)
+        oracle_check(orc, L, k0, r0, [0, 37])
+        oracle_check(orc, L, k1, r1, [63])
+    finally:
+        L.close()
+
+
+def test_batched_4gib_autotuned_and_graph(torch_cuda, orc):
+    """N=2^22 x 1 KiB (4 GiB), 256 queries of domain 2^22: autotuned launch shape, replayed
+    from a captured CUDA graph."""
+    torch = torch_cuda
+    L = Loaded(torch, workloads.batched_4gib())
+    try:
+        b, k0, k1 = L.batches[0]
+        n = len(k0)
+        blob, offs = impir.pack_keys(k0)
+        d_keys = torch.from_numpy(np.frombuffer(blob, np.uint8).copy()).cuda()
+        d_off = torch.from_numpy(offs.view(np.int32).copy()).cuda()
+        d_out = torch.zeros((n, 1024), dtype=torch.uint8, device="cuda")
+        wsb = impir.impir_workspace_bytes(n, L.stride)
+        d_ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+        s = torch.cuda.Stream()
+        impir.impir_autotune(L.h, d_keys, d_off, 64, d_out, d_ws, wsb, s)   # tune on a 64-query slice
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            impir.impir_answer_async(L.h, d_keys, d_off, n, d_out, d_ws, wsb, s)   # warm (outside capture)
+            s.synchronize()
+            with torch.cuda.graph(g, stream=s):
+                impir.impir_answer_async(L.h, d_keys, d_off, n, d_out, d_ws, wsb, s)
+        d_out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        r0 = d_out.cpu().numpy()
+        r1 = L.answer_async(k1)
+        L.check_reconstruction(r0, r1, b.alphas)
+        oracle_check(orc, L, k0, r0, [5])
+        oracle_check(orc, L, k1, r1, [200])
+    finally:
+        L.close()
+
+
+def test_uneven_8gib_batched_and_plain(torch_cuda, orc):
+    """N=2^25 x 256 B (8 GiB), 1024 queries in batches of 1..512 mixing domains 2^23..2^25
+    over DB prefixes; the one-query-per-launch form gives the same bits."""
+    L = Loaded(torch_cuda, workloads.uneven_8gib())
+    try:
+        sampled = {}
+        for bi, (b, k0, k1) in enumerate(L.batches):
+            r0 = L.answer_async(k0)
+            r1 = L.answer_async(k1)
+            L.check_reconstruction(r0, r1, b.alphas)
+            for i, m in enumerate(b.ms):
+                if m not in sampled:
+                    sampled[m] = (k0[i], r0[i])
+            if bi == 0:
+                cfg = impir.impir_get_config(L.h, len(k0)).as_dict()
+                impir.impir_set_config(L.h, cfg["lane_bits"], 1, cfg["warps_per_cta"], 1)
+                p0 = L.answer_async(k0[:48])
+                impir.impir_set_config(L.h, cfg["lane_bits"], cfg["queries_per_warp"], cfg["warps_per_cta"], 0)
+                assert np.array_equal(p0, r0[:48])
+        assert set(sampled) == {23, 24, 25}
+        for m, (k, r) in sorted(sampled.items()):
+            assert r.tobytes() == orc.answer(k, L.db, L.w.n_records, L.w.record_bytes, threads=16), m
+    finally:
+        L.close()
