@@ -165,6 +165,32 @@ impir_status impir_reconstruct(const uint8_t* r0, const uint8_t* r1, uint32_t re
 /* Thread-local message describing the last failure on this thread ("" if none). */
 const char* impir_last_error(void);
 
+/* ---- Answering without any allocation ----
+ * The paper has no counterpart to this call; it exists for callers that may not allocate
+ * device memory at the moment they answer (code running inside an allocator or memory-pool
+ * callback, a process whose device memory a framework reserved up front, or a path that must
+ * not risk the implicit synchronization of cudaMalloc/cudaFree). It computes exactly what
+ * impir_answer_async computes, on a database given by pointer (no handle), with keys, key
+ * offsets and answers in caller-owned device memory, but takes no workspace: its scratch is
+ * a fixed array of IMPIR_NOALLOC_SCRATCH_BYTES in the library's device memory, present on
+ * every GPU that loads the library until the process exits.
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - The batch must fit: the workspace of impir_workspace_bytes(n_queries, stride_bytes)
+ *     must be <= IMPIR_NOALLOC_SCRATCH_BYTES, else EINVAL and nothing is launched.
+ *   - The first call on a device does a one-time set-up for that device (it looks up the
+ *     scratch array's device address and uploads a 1 KiB AES table); make that first call
+ *     before any stream capture.
+ *   - Every call shares the one scratch array, which keeps the last call's contents (each
+ *     call clears what must start at zero). Calls whose kernels overlap on the GPU race on
+ *     it: issue them on one stream, or otherwise order them.
+ * d_records: n_records records, record j at d_records + j * stride_bytes (stride a multiple
+ * of 16, >= record_bytes, padding bytes zero, 16-byte aligned). Malformed keys give zero
+ * answers, as in impir_answer_async (their status is not reported here). */
+#define IMPIR_NOALLOC_SCRATCH_BYTES (8u << 20)
+impir_status impir_answer_noalloc(const void* d_records, uint64_t n_records, uint32_t record_bytes,
+                                  uint32_t stride_bytes, const uint8_t* d_keys, const uint32_t* d_key_offsets,
+                                  uint32_t n_queries, uint8_t* d_out, void* cuda_stream);
+
 /* ---- Kernel timing (measurement support; off by default) ----
  * While enabled, each fused EvalAll + dpXOR launch is bracketed by two CUDA events recorded
  * on the stream it is launched on. impir_timing_read waits for those events and returns the

@@ -29,7 +29,7 @@ EXPORTS = [
     "impir_key_bytes", "impir_db_load", "impir_db_attach", "impir_db_free", "impir_db_info", "impir_answer",
     "impir_workspace_bytes", "impir_answer_async", "impir_workspace_status", "impir_get_config",
     "impir_set_config", "impir_autotune", "dpf_gen", "impir_reconstruct", "impir_last_error",
-    "impir_device_sm_count", "impir_timing_enable", "impir_timing_read",
+    "impir_device_sm_count", "impir_timing_enable", "impir_timing_read", "impir_answer_noalloc",
 ]
 
 
@@ -85,6 +85,8 @@ def lib():
                 "impir_last_error": (ctypes.c_char_p, []),
                 "impir_device_sm_count": (ctypes.c_int32, []),
                 "impir_timing_enable": (ctypes.c_int, [ctypes.c_int]),
+                "impir_answer_noalloc": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, vp, vp,
+                                                        ctypes.c_uint32, vp, vp]),
                 "impir_timing_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64),
                                                      ctypes.POINTER(ctypes.c_uint64)]),
             }
@@ -228,6 +230,17 @@ def impir_last_error() -> str:
 
 def impir_device_sm_count() -> int:
     return int(lib().impir_device_sm_count())
+
+
+IMPIR_NOALLOC_SCRATCH_BYTES = 8 << 20
+
+
+def impir_answer_noalloc(d_records, n_records: int, record_bytes: int, stride_bytes: int, d_keys, d_key_offsets,
+                         n_queries: int, d_out, stream=None) -> None:
+    """Answer without allocating: scratch lives in a fixed device array inside the library."""
+    _check(lib().impir_answer_noalloc(_dev(d_records), n_records, record_bytes, stride_bytes, _dev(d_keys),
+                                      _dev(d_key_offsets), n_queries, _dev(d_out), _stream(stream)),
+           "impir_answer_noalloc")
 
 
 def impir_timing_enable(enable: bool = True) -> None:

@@ -18,8 +18,18 @@
 using namespace impir;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+namespace impir {
+// Records a message for impir_last_error (used by units outside this file).
+impir_status set_error(impir_status st, const char* msg) {
+    g_err = msg;
+    return st;
+}
+}  // namespace impir
+
+namespace {
 
 impir_status fail(impir_status st, const char* fmt, ...) {
     char buf[512];
