@@ -44,6 +44,8 @@ def parse_args():
     p.add_argument("--no-plain", action="store_true", help="skip the one-query-per-launch comparison")
     p.add_argument("--no-tune", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=2, help="queries in the oracle's timed sample")
+    p.add_argument("--no-serving", action="store_true", help="skip the serving sweep (three resident DBs)")
+    p.add_argument("--serving-requests", type=int, default=2000, help="requests per arrival rate")
     return p.parse_args()
 
 
@@ -199,6 +201,79 @@ def run_reference(args, world, rank):
     }), flush=True)
 
 
+# ---------------------------------------------------------------- serving sweep
+
+def run_serving(args, impir, workloads):
+    """Three resident DBs, Poisson arrivals at each rate, uniform DB and target; continuous
+    batching by the library's server. Returns per-rate throughput and p50/p99 latency."""
+    import threading
+    dbs = []
+    for i, (n, b) in enumerate(workloads.SERVING_DBS):
+        db = workloads.make_db(n, b, seed=900 + i)
+        dbs.append((impir.impir_db_load(db, n, b), db, n, b))
+    server = impir.impir_server_create(max_batch=256, streams=4, max_record_bytes=512,
+                                       accumulator_budget=4 * 256 * 512)
+    points = []
+    try:
+        for rate in workloads.SERVING_RATES:
+            arr = workloads.poisson_arrivals(rate, args.serving_requests, dbs=workloads.SERVING_DBS)
+            keys = []
+            for i in range(len(arr.t)):
+                d = int(arr.db[i])
+                m = dbs[d][2].bit_length() - 1
+                keys.append(impir.dpf_gen(int(arr.alpha[i]), m, impir.IMPIR_PRF_AES_KEYED, arr.seeds[i])[0])
+            done = {}
+            before = impir.impir_server_stats(server)
+            t_sub = [0.0] * len(keys)
+
+            def client():
+                t0 = time.perf_counter()
+                for i, k in enumerate(keys):
+                    due = float(arr.t[i])
+                    while True:
+                        left = due - (time.perf_counter() - t0)
+                        if left <= 0:
+                            break
+                        if left > 2e-4:
+                            time.sleep(left - 1e-4)
+                    t_sub[i] = time.perf_counter()
+                    impir.impir_server_submit(server, dbs[int(arr.db[i])][0], k, i)
+
+            th = threading.Thread(target=client)
+            t_start = time.perf_counter()
+            th.start()
+            while len(done) < len(keys):
+                r = impir.impir_server_take(server, 2_000_000)
+                if r is None:
+                    break
+                done[r["tag"]] = (r, time.perf_counter())
+            th.join()
+            t_end = max(t for _, t in done.values())
+            after = impir.impir_server_stats(server)
+            lat = np.array([r["latency_ns"] for r, _ in done.values()]) / 1e6
+            bad = checked = 0
+            for i in range(0, len(keys), max(1, len(keys) // 24)):
+                checked += 1
+                h, _, _, b = dbs[int(arr.db[i])]
+                bad += int(done[i][0]["answer"] != impir.impir_answer(h, keys[i], 1, b)[0].tobytes())
+            points.append({
+                "offered_req_s": rate, "requests": len(keys), "completed": len(done),
+                "submit_rate_req_s": len(keys) / max(1e-9, t_sub[-1] - t_sub[0]),
+                "queries_per_s": len(done) / (t_end - t_start),
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_batch": (after["queries"] - before["queries"]) / max(1, after["batches"] - before["batches"]),
+                "max_inflight_batches": after["max_inflight_batches"],
+                "sampled_vs_alone": {"checked": checked, "mismatches": bad},
+            })
+    finally:
+        impir.impir_server_destroy(server)
+        for h, *_ in dbs:
+            impir.impir_db_free(h)
+    return {"dbs": [f"2^{n.bit_length() - 1} x {b} B" for n, b in workloads.SERVING_DBS],
+            "server": {"max_batch": 256, "streams": 4, "accumulator_budget": 4 * 256 * 512},
+            "points": points}
+
+
 # ---------------------------------------------------------------- our arm
 
 def main():
@@ -352,6 +427,10 @@ def main():
                "sample": f"{len(qs)} queries of the workload (m={[batches[b]['ms'][i] for b, i in qs]}), "
                          f"threaded oracle, {dt:.1f} s", "bit_identical_to_gpu": bool(agree)}
 
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = run_serving(args, impir, workloads)
+
     if rank == 0:
         out = {
             "metric": "PIR queries/s (DPF eval+dpXOR) at 8 GiB DB", "value": value, "unit": "queries/s",
@@ -375,6 +454,7 @@ def main():
             "one_query_per_launch": plain,
             "parity": {"reconstructed_ok": nq - bad, "queries": nq},
             "cpu_baseline": cpu,
+            "serving": serving,
             "setup_s": setup_s,
         }
         print(json.dumps(out), flush=True)

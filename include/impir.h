@@ -148,6 +148,51 @@ impir_status impir_autotune(int32_t db_handle, const uint8_t* d_keys, const uint
                             uint32_t n_queries, uint8_t* d_out, void* d_workspace, size_t workspace_bytes,
                             void* cuda_stream, impir_config* best);
 
+/* ---- Serving: continuous batching over resident databases (§3.4 query batching) ----
+ * A server owns `streams` CUDA streams, each with device buffers for one batch of up to
+ * max_batch queries. Any thread may submit requests (one key for one registered database,
+ * tagged by the caller). A dispatcher thread admits the oldest pending requests into the next
+ * batch as soon as a stream is free and the per-query accumulator memory in flight stays
+ * within accumulator_budget (a batch of n queries on a database of stride S holds n*S bytes),
+ * taking further pending requests for the same database in arrival order; it launches the
+ * fused answer on that stream, so batches that arrive while others run overlap on the device.
+ * Each result is the same as answering that key alone. No kernel waits on anything; the
+ * dispatcher polls batch completion events on the host. */
+typedef struct impir_server impir_server;
+typedef struct {
+    uint32_t max_batch;          /* most queries one launch takes (>= 1) */
+    uint32_t streams;            /* batches in flight at once, one CUDA stream each (1..64) */
+    uint32_t max_record_bytes;   /* largest record of any database the server will answer */
+    uint32_t reserved;           /* zero */
+    uint64_t accumulator_budget; /* device bytes of in-flight per-query accumulators (>= one stride) */
+} impir_server_config;
+
+/* Creates a server on the current device (allocates its stream buffers up front).
+ * EINVAL: bad configuration; ENOMEM: buffers could not be allocated. */
+impir_status impir_server_create(const impir_server_config* cfg, impir_server** server);
+
+/* Queues one request: `key` is host memory holding one wire key (copied before return),
+ * `db_handle` a loaded database, `tag` any caller value returned with the answer.
+ * EINVAL: malformed key header, unknown database, or records beyond max_record_bytes. */
+impir_status impir_server_submit(impir_server* server, int32_t db_handle, const uint8_t* key, uint64_t tag);
+
+/* Waits up to timeout_us for any finished request and returns it: its tag, database, answer
+ * (copied into `answer`, record_bytes of its database, at most answer_capacity), the latency
+ * from submit to completion in nanoseconds, and the size of the batch it ran in.
+ * ETIMEOUT: nothing finished in time. A request that failed returns its failure status
+ * (with its tag filled in). */
+impir_status impir_server_take(impir_server* server, uint32_t timeout_us, uint64_t* tag, int32_t* db_handle,
+                               uint8_t* answer, uint32_t answer_capacity, uint32_t* answer_bytes,
+                               uint64_t* latency_ns, uint32_t* batch_size);
+
+/* Counters: batches launched, queries launched, most batches in flight at once, requests
+ * still waiting for admission. */
+impir_status impir_server_stats(impir_server* server, uint64_t* batches, uint64_t* queries,
+                                uint32_t* max_inflight_batches, uint32_t* pending);
+
+/* Stops the dispatcher after the batches in flight finish, and frees the server. */
+impir_status impir_server_destroy(impir_server* server);
+
 /* ---- Client side, used by tests (§3.1 Gen, §2.3 reconstruction) ---- */
 
 /* Gen(alpha) for domain bits m: writes key0 and key1 (impir_key_bytes(m) each) such that

@@ -30,6 +30,7 @@ EXPORTS = [
     "impir_workspace_bytes", "impir_answer_async", "impir_workspace_status", "impir_get_config",
     "impir_set_config", "impir_autotune", "dpf_gen", "impir_reconstruct", "impir_last_error",
     "impir_device_sm_count", "impir_timing_enable", "impir_timing_read", "impir_answer_noalloc",
+    "impir_server_create", "impir_server_submit", "impir_server_take", "impir_server_stats", "impir_server_destroy",
 ]
 
 
@@ -45,6 +46,11 @@ class impir_config(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+class impir_server_config(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_uint32), ("streams", ctypes.c_uint32), ("max_record_bytes", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("accumulator_budget", ctypes.c_uint64)]
 
 
 _lock = threading.Lock()
@@ -85,6 +91,15 @@ def lib():
                 "impir_last_error": (ctypes.c_char_p, []),
                 "impir_device_sm_count": (ctypes.c_int32, []),
                 "impir_timing_enable": (ctypes.c_int, [ctypes.c_int]),
+                "impir_server_create": (ctypes.c_int, [ctypes.POINTER(impir_server_config), ctypes.POINTER(ctypes.c_void_p)]),
+                "impir_server_submit": (ctypes.c_int, [vp, ctypes.c_int32, u8p, ctypes.c_uint64]),
+                "impir_server_take": (ctypes.c_int, [vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
+                                                     ctypes.POINTER(ctypes.c_int32), u8p, ctypes.c_uint32,
+                                                     ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64),
+                                                     ctypes.POINTER(ctypes.c_uint32)]),
+                "impir_server_stats": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                                      ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
+                "impir_server_destroy": (ctypes.c_int, [vp]),
                 "impir_answer_noalloc": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, vp, vp,
                                                         ctypes.c_uint32, vp, vp]),
                 "impir_timing_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64),
@@ -233,6 +248,43 @@ def impir_device_sm_count() -> int:
 
 
 IMPIR_NOALLOC_SCRATCH_BYTES = 8 << 20
+
+
+def impir_server_create(max_batch: int, streams: int, max_record_bytes: int, accumulator_budget: int) -> int:
+    cfg = impir_server_config(max_batch, streams, max_record_bytes, 0, accumulator_budget)
+    h = ctypes.c_void_p()
+    _check(lib().impir_server_create(ctypes.byref(cfg), ctypes.byref(h)), "impir_server_create")
+    return h.value
+
+
+def impir_server_submit(server: int, db: int, key: bytes, tag: int) -> None:
+    _, kp = _host(key)
+    _check(lib().impir_server_submit(ctypes.c_void_p(server), db, kp, tag), "impir_server_submit")
+
+
+def impir_server_take(server: int, timeout_us: int, answer_capacity: int = 1 << 16):
+    """Next finished request: dict(tag, db, answer, latency_ns, batch) or None on timeout."""
+    tag, db, nb, lat, bs = ctypes.c_uint64(), ctypes.c_int32(), ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_uint32()
+    buf = np.zeros(answer_capacity, np.uint8)
+    st = lib().impir_server_take(ctypes.c_void_p(server), timeout_us, ctypes.byref(tag), ctypes.byref(db),
+                                 ctypes.c_void_p(buf.ctypes.data), answer_capacity, ctypes.byref(nb),
+                                 ctypes.byref(lat), ctypes.byref(bs))
+    if st == IMPIR_ETIMEOUT:
+        return None
+    _check(st, "impir_server_take")
+    return {"tag": tag.value, "db": db.value, "answer": buf[: nb.value].tobytes(), "latency_ns": lat.value,
+            "batch": bs.value}
+
+
+def impir_server_stats(server: int) -> dict:
+    b, q, mi, p = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().impir_server_stats(ctypes.c_void_p(server), ctypes.byref(b), ctypes.byref(q), ctypes.byref(mi),
+                                    ctypes.byref(p)), "impir_server_stats")
+    return {"batches": b.value, "queries": q.value, "max_inflight_batches": mi.value, "pending": p.value}
+
+
+def impir_server_destroy(server: int) -> None:
+    _check(lib().impir_server_destroy(ctypes.c_void_p(server)), "impir_server_destroy")
 
 
 def impir_answer_noalloc(d_records, n_records: int, record_bytes: int, stride_bytes: int, d_keys, d_key_offsets,
