@@ -43,6 +43,8 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true", help="skip the one-query-per-launch comparison")
     p.add_argument("--no-tune", action="store_true")
+    p.add_argument("--config", default=None,
+                   help="fixed launch shape lane_bits,queries_per_warp,warps_per_cta (skips autotuning)")
     p.add_argument("--cpu-sample", type=int, default=2, help="queries in the oracle's timed sample")
     p.add_argument("--no-serving", action="store_true", help="skip the serving sweep (three resident DBs)")
     p.add_argument("--serving-requests", type=int, default=2000, help="requests per arrival rate")
@@ -327,7 +329,10 @@ def main():
 
     # autotune on the largest batch (outside the timed region)
     tuned = None
-    if not args.no_tune:
+    if args.config:
+        lb, qpw, wpc = (int(x) for x in args.config.split(","))
+        impir.impir_set_config(dbh, lb, qpw, wpc, 0)
+    elif not args.no_tune:
         big = max(batches, key=lambda bt: bt["n"])
         tuned = impir.impir_autotune(dbh, big["d_keys0"], big["d_off"], big["n"], big["d_out"], big["d_ws"],
                                      big["wsb"], stream).as_dict()

@@ -91,10 +91,12 @@ __device__ __forceinline__ uint32_t sub_rot(uint32_t w, uint32_t L) {
 // lsb of S[byte 0 of v].
 __device__ __forceinline__ uint32_t sbox0_lsb(uint32_t v, uint32_t L) { return T<2>(tix(v, L, 0)) & 1u; }
 
-__device__ __forceinline__ constexpr uint32_t rcon(int r) {
-    return r == 1 ? 0x01u : r == 2 ? 0x02u : r == 3 ? 0x04u : r == 4 ? 0x08u : r == 5 ? 0x10u
-         : r == 6 ? 0x20u : r == 7 ? 0x40u : r == 8 ? 0x80u : r == 9 ? 0x1bu : 0x36u;
-}
+// Next round constant: doubling in GF(2^8) (0x01, 0x02, ..., 0x80, 0x1b, 0x36).
+__device__ __forceinline__ uint32_t rc_next(uint32_t rc) { return (rc << 1) ^ ((rc >> 7) * 0x11bu); }
+
+// The round loops below are kept rolled: the fully unrolled PRF variants overflow the
+// instruction cache of the persistent kernel's hot loop.
+
 
 struct Key4 {
     uint32_t a, b, c, d;
@@ -126,15 +128,17 @@ __device__ __forceinline__ void keyed_round1(const Blk p, uint32_t L, const Key4
 // Both children's PRF outputs (128-bit each) of parent seed p.
 __device__ __forceinline__ void keyed_pair(const Blk p, uint32_t L, Blk& a, Blk& b) {
     Key4 k{p.x, p.y, p.z, p.w};
-    ks_next(k, rcon(1), L);
+    uint32_t rc = 1;
+    ks_next(k, rc, L);
     keyed_round1(p, L, k, a, b);
-#pragma unroll
+#pragma unroll 1
     for (int r = 2; r <= 9; ++r) {
-        ks_next(k, rcon(r), L);
+        rc = rc_next(rc);
+        ks_next(k, rc, L);
         a = aes_round(a, L, k.a, k.b, k.c, k.d);
         b = aes_round(b, L, k.a, k.b, k.c, k.d);
     }
-    ks_next(k, rcon(10), L);
+    ks_next(k, 0x36u, L);
     a = aes_final(a, L, k.a, k.b, k.c, k.d);
     b = aes_final(b, L, k.a, k.b, k.c, k.d);
 }
@@ -145,15 +149,17 @@ __device__ __forceinline__ void keyed_pair(const Blk p, uint32_t L, Blk& a, Blk&
 __device__ __forceinline__ uint32_t keyed_leaf_bits(const Blk p, uint32_t L) {
     Key4 k{p.x, p.y, p.z, p.w};
     Blk a, b;
-    ks_next(k, rcon(1), L);
+    uint32_t rc = 1;
+    ks_next(k, rc, L);
     keyed_round1(p, L, k, a, b);
-#pragma unroll
+#pragma unroll 1
     for (int r = 2; r <= 8; ++r) {
-        ks_next(k, rcon(r), L);
+        rc = rc_next(rc);
+        ks_next(k, rc, L);
         a = aes_round(a, L, k.a, k.b, k.c, k.d);
         b = aes_round(b, L, k.a, k.b, k.c, k.d);
     }
-    ks_next(k, rcon(9), L);
+    ks_next(k, 0x1bu, L);
     const uint32_t a9 = aes_round_col0(a, L, k.a);
     const uint32_t b9 = aes_round_col0(b, L, k.a);
     const uint32_t kbit = (k.a ^ sbox0_lsb(k.d >> 8, L)) & 1u;  // lsb(0x36) = 0
@@ -164,12 +170,14 @@ __device__ __forceinline__ uint32_t keyed_leaf_bits(const Blk p, uint32_t L) {
 __device__ __forceinline__ Blk keyed_one(const Blk p, uint32_t x, uint32_t L) {
     Key4 k{p.x, p.y, p.z, p.w};
     Blk s{p.x ^ x, p.y, p.z, p.w};
-#pragma unroll
+    uint32_t rc = 1;
+#pragma unroll 1
     for (int r = 1; r <= 9; ++r) {
-        ks_next(k, rcon(r), L);
+        ks_next(k, rc, L);
+        rc = rc_next(rc);
         s = aes_round(s, L, k.a, k.b, k.c, k.d);
     }
-    ks_next(k, rcon(10), L);
+    ks_next(k, 0x36u, L);
     return aes_final(s, L, k.a, k.b, k.c, k.d);
 }
 
@@ -178,7 +186,7 @@ __device__ __forceinline__ Blk keyed_one(const Blk p, uint32_t x, uint32_t L) {
 __device__ __forceinline__ void mmo_pair(const Blk p, uint32_t L, const uint32_t (&rk)[2][44], Blk& a, Blk& b) {
     a = {p.x ^ rk[0][0], p.y ^ rk[0][1], p.z ^ rk[0][2], p.w ^ rk[0][3]};
     b = {p.x ^ rk[1][0], p.y ^ rk[1][1], p.z ^ rk[1][2], p.w ^ rk[1][3]};
-#pragma unroll
+#pragma unroll 1
     for (int r = 1; r <= 9; ++r) {
         a = aes_round(a, L, rk[0][4 * r], rk[0][4 * r + 1], rk[0][4 * r + 2], rk[0][4 * r + 3]);
         b = aes_round(b, L, rk[1][4 * r], rk[1][4 * r + 1], rk[1][4 * r + 2], rk[1][4 * r + 3]);
@@ -190,7 +198,7 @@ __device__ __forceinline__ void mmo_pair(const Blk p, uint32_t L, const uint32_t
 __device__ __forceinline__ uint32_t mmo_leaf_bits(const Blk p, uint32_t L, const uint32_t (&rk)[2][44]) {
     Blk a = {p.x ^ rk[0][0], p.y ^ rk[0][1], p.z ^ rk[0][2], p.w ^ rk[0][3]};
     Blk b = {p.x ^ rk[1][0], p.y ^ rk[1][1], p.z ^ rk[1][2], p.w ^ rk[1][3]};
-#pragma unroll
+#pragma unroll 1
     for (int r = 1; r <= 8; ++r) {
         a = aes_round(a, L, rk[0][4 * r], rk[0][4 * r + 1], rk[0][4 * r + 2], rk[0][4 * r + 3]);
         b = aes_round(b, L, rk[1][4 * r], rk[1][4 * r + 1], rk[1][4 * r + 2], rk[1][4 * r + 3]);
@@ -205,7 +213,7 @@ __device__ __forceinline__ uint32_t mmo_leaf_bits(const Blk p, uint32_t L, const
 __device__ __forceinline__ Blk mmo_one(const Blk p, uint32_t x, uint32_t L, const uint32_t (&rk)[2][44]) {
     Blk s = {p.x ^ (x ? rk[1][0] : rk[0][0]), p.y ^ (x ? rk[1][1] : rk[0][1]), p.z ^ (x ? rk[1][2] : rk[0][2]),
              p.w ^ (x ? rk[1][3] : rk[0][3])};
-#pragma unroll
+#pragma unroll 1
     for (int r = 1; r <= 9; ++r)
         s = aes_round(s, L, x ? rk[1][4 * r] : rk[0][4 * r], x ? rk[1][4 * r + 1] : rk[0][4 * r + 1],
                       x ? rk[1][4 * r + 2] : rk[0][4 * r + 2], x ? rk[1][4 * r + 3] : rk[0][4 * r + 3]);
@@ -309,6 +317,7 @@ __device__ __forceinline__ uint4 shfl_xor4(const uint4 v, int off) {
 }
 
 // dpXOR of one warp tile for the group's queries: records [tile_base, tile_base + nrec).
+// Selection bits are read one 32-bit word (32 records) per query at a time.
 template <int QC, int NK>
 __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_base, uint32_t nrec,
                                           const uint32_t* bits, uint32_t count, const uint32_t* qidx, uint4* acc_out,
@@ -323,21 +332,30 @@ __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_ba
 #pragma unroll
         for (int q = 0; q < QC; ++q) acc[q] = make_uint4(0, 0, 0, 0);
         const uint4* base = P.db + tile_base * W + lk;
-        constexpr int U = 4;
-        for (uint32_t r0 = 0; r0 < nrec; r0 += U * R) {
-            uint4 v[U];
+        for (uint32_t c0 = 0; c0 < nrec; c0 += 32) {
+            uint32_t sel[QC];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint32_t r = r0 + u * R + lr;
-                v[u] = (on && r < nrec) ? ld_db(base + size_t(r) * W) : make_uint4(0, 0, 0, 0);
-            }
+            for (int q = 0; q < QC; ++q) sel[q] = bits[q * bw + (c0 >> 5)] >> lr;  // bit i*R of sel: record c0+i*R+lr
+            const uint32_t nloc = min(32u, nrec - c0);
+            if (R == 1) {
+                // one record per step for the whole warp: its selection bits are warp-uniform
+#pragma unroll 4
+                for (uint32_t i = 0; i < nloc; ++i) {
+                    const uint4 v = on ? ld_db(base + size_t(c0 + i) * W) : make_uint4(0, 0, 0, 0);
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint32_t r = min(r0 + u * R + lr, nrec - 1);
+                    for (int q = 0; q < QC; ++q)
+                        if ((sel[q] >> i) & 1u) acc[q] = bxor4(acc[q], v);
+                }
+            } else {
+#pragma unroll 4
+                for (uint32_t i = 0; i < 32; i += R) {
+                    const uint32_t r = c0 + i + lr;
+                    const uint4 v = (on && i + lr < nloc) ? ld_db(base + size_t(r) * W) : make_uint4(0, 0, 0, 0);
 #pragma unroll
-                for (int q = 0; q < QC; ++q) {
-                    const uint32_t msk = 0u - ((bits[q * bw + (r >> 5)] >> (r & 31)) & 1u);
-                    xor_masked(acc[q], v[u], msk);
+                    for (int q = 0; q < QC; ++q) {
+                        const uint32_t msk = uint32_t(int32_t(sel[q] << (31u - i)) >> 31);
+                        xor_masked(acc[q], v, msk);
+                    }
                 }
             }
         }
@@ -355,26 +373,33 @@ __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_ba
                 if (uint32_t(q) < count) red_xor(acc_out + size_t(qidx[q]) * W + lk, acc[q]);
         }
     } else {
-        // W > 32: the whole warp reads one record per step, NK words per lane, in column passes
-        for (uint32_t c0 = 0; c0 < W; c0 += 32 * NK) {
+        // W > 32: the whole warp reads one record per step, NK words per lane, in column
+        // passes; a record's selection bits are warp-uniform, so unselected records skip the XOR
+        for (uint32_t k0 = 0; k0 < W; k0 += 32 * NK) {
             uint4 acc[QC][NK];
 #pragma unroll
             for (int q = 0; q < QC; ++q)
 #pragma unroll
                 for (int c = 0; c < NK; ++c) acc[q][c] = make_uint4(0, 0, 0, 0);
-            for (uint32_t r = 0; r < nrec; ++r) {
-                uint4 v[NK];
-                const uint4* rec = P.db + (tile_base + r) * W;
+            for (uint32_t c0 = 0; c0 < nrec; c0 += 32) {
+                uint32_t sel[QC];
 #pragma unroll
-                for (int c = 0; c < NK; ++c) {
-                    const uint32_t k = c0 + lane + 32 * c;
-                    v[c] = k < W ? ld_db(rec + k) : make_uint4(0, 0, 0, 0);
-                }
+                for (int q = 0; q < QC; ++q) sel[q] = bits[q * bw + (c0 >> 5)];
+                const uint32_t nloc = min(32u, nrec - c0);
+#pragma unroll 2
+                for (uint32_t i = 0; i < nloc; ++i) {
+                    uint4 v[NK];
+                    const uint4* rec = P.db + (tile_base + c0 + i) * W;
 #pragma unroll
-                for (int q = 0; q < QC; ++q) {
-                    const uint32_t msk = 0u - ((bits[q * bw + (r >> 5)] >> (r & 31)) & 1u);
+                    for (int c = 0; c < NK; ++c) {
+                        const uint32_t k = k0 + lane + 32 * c;
+                        v[c] = k < W ? ld_db(rec + k) : make_uint4(0, 0, 0, 0);
+                    }
 #pragma unroll
-                    for (int c = 0; c < NK; ++c) xor_masked(acc[q][c], v[c], msk);
+                    for (int q = 0; q < QC; ++q)
+                        if ((sel[q] >> i) & 1u)
+#pragma unroll
+                            for (int c = 0; c < NK; ++c) acc[q][c] = bxor4(acc[q][c], v[c]);
                 }
             }
 #pragma unroll
@@ -382,7 +407,7 @@ __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_ba
                 if (uint32_t(q) < count)
 #pragma unroll
                     for (int c = 0; c < NK; ++c) {
-                        const uint32_t k = c0 + lane + 32 * c;
+                        const uint32_t k = k0 + lane + 32 * c;
                         if (k < W) red_xor(acc_out + size_t(qidx[q]) * W + k, acc[q][c]);
                     }
         }
