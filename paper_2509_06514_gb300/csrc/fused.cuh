@@ -82,17 +82,21 @@ __device__ __forceinline__ uint32_t aes_round_col0(const Blk s, uint32_t L, uint
     return T<0>(tix(s.x, L, 0)) ^ T<1>(tix(s.y, L, 1)) ^ T<2>(tix(s.z, L, 2)) ^ T<3>(tix(s.w, L, 3)) ^ k0;
 }
 
-// SubWord(RotWord(w)) of the key schedule (FIPS-197 §5.2) on a little-endian word.
+// SubWord(RotWord(w)) of the key schedule (FIPS-197 §5.2) on a little-endian word: byte i
+// of the result is S[byte i+1 of w]; each lookup's S byte already sits in its target byte
+// position, so three byte permutes assemble the word.
 __device__ __forceinline__ uint32_t sub_rot(uint32_t w, uint32_t L) {
-    return (T<2>(tix(w, L, 1)) & 0xffu) ^ (T<3>(tix(w, L, 2)) & 0xff00u) ^ (T<0>(tix(w, L, 3)) & 0xff0000u) ^
-           (T<1>(tix(w, L, 0)) & 0xff000000u);
+    const uint32_t lo = __byte_perm(T<2>(tix(w, L, 1)), T<3>(tix(w, L, 2)), 0x0050u);
+    const uint32_t hi = __byte_perm(T<0>(tix(w, L, 3)), T<1>(tix(w, L, 0)), 0x7200u);
+    return __byte_perm(lo, hi, 0x7610u);
 }
 
 // lsb of S[byte 0 of v].
 __device__ __forceinline__ uint32_t sbox0_lsb(uint32_t v, uint32_t L) { return T<2>(tix(v, L, 0)) & 1u; }
 
-// Next round constant: doubling in GF(2^8) (0x01, 0x02, ..., 0x80, 0x1b, 0x36).
-__device__ __forceinline__ uint32_t rc_next(uint32_t rc) { return (rc << 1) ^ ((rc >> 7) * 0x11bu); }
+// Round constants of the key schedule (FIPS-197 §5.2), indexed by round; read from the
+// constant cache so the rolled round loops spend no ALU work on them.
+__constant__ uint32_t c_rcon[11] = {0x00, 0x01, 0x02, 0x04, 0x08, 0x10, 0x20, 0x40, 0x80, 0x1b, 0x36};
 
 // The round loops below are kept rolled: the fully unrolled PRF variants overflow the
 // instruction cache of the persistent kernel's hot loop.
@@ -125,22 +129,21 @@ __device__ __forceinline__ void keyed_round1(const Blk p, uint32_t L, const Key4
     b.w = a.w;
 }
 
-// Both children's PRF outputs (128-bit each) of parent seed p.
-__device__ __forceinline__ void keyed_pair(const Blk p, uint32_t L, Blk& a, Blk& b) {
+// Both children of parent seed p: PRF_p(0) ^ ca and PRF_p(1) ^ cb (the correction words
+// are folded into the last AddRoundKey).
+__device__ __forceinline__ void keyed_pair(const Blk p, uint32_t L, const Blk ca, const Blk cb, Blk& a, Blk& b) {
     Key4 k{p.x, p.y, p.z, p.w};
-    uint32_t rc = 1;
-    ks_next(k, rc, L);
+    ks_next(k, 0x01u, L);
     keyed_round1(p, L, k, a, b);
 #pragma unroll 1
     for (int r = 2; r <= 9; ++r) {
-        rc = rc_next(rc);
-        ks_next(k, rc, L);
+        ks_next(k, c_rcon[r], L);
         a = aes_round(a, L, k.a, k.b, k.c, k.d);
         b = aes_round(b, L, k.a, k.b, k.c, k.d);
     }
     ks_next(k, 0x36u, L);
-    a = aes_final(a, L, k.a, k.b, k.c, k.d);
-    b = aes_final(b, L, k.a, k.b, k.c, k.d);
+    a = aes_final(a, L, k.a ^ ca.x, k.b ^ ca.y, k.c ^ ca.z, k.d ^ ca.w);
+    b = aes_final(b, L, k.a ^ cb.x, k.b ^ cb.y, k.c ^ cb.z, k.d ^ cb.w);
 }
 
 // lsb of both PRF outputs: rounds 1-8 in full, then only what byte 0 of the output needs:
@@ -149,13 +152,11 @@ __device__ __forceinline__ void keyed_pair(const Blk p, uint32_t L, Blk& a, Blk&
 __device__ __forceinline__ uint32_t keyed_leaf_bits(const Blk p, uint32_t L) {
     Key4 k{p.x, p.y, p.z, p.w};
     Blk a, b;
-    uint32_t rc = 1;
-    ks_next(k, rc, L);
+    ks_next(k, 0x01u, L);
     keyed_round1(p, L, k, a, b);
 #pragma unroll 1
     for (int r = 2; r <= 8; ++r) {
-        rc = rc_next(rc);
-        ks_next(k, rc, L);
+        ks_next(k, c_rcon[r], L);
         a = aes_round(a, L, k.a, k.b, k.c, k.d);
         b = aes_round(b, L, k.a, k.b, k.c, k.d);
     }
@@ -170,11 +171,9 @@ __device__ __forceinline__ uint32_t keyed_leaf_bits(const Blk p, uint32_t L) {
 __device__ __forceinline__ Blk keyed_one(const Blk p, uint32_t x, uint32_t L) {
     Key4 k{p.x, p.y, p.z, p.w};
     Blk s{p.x ^ x, p.y, p.z, p.w};
-    uint32_t rc = 1;
 #pragma unroll 1
     for (int r = 1; r <= 9; ++r) {
-        ks_next(k, rc, L);
-        rc = rc_next(rc);
+        ks_next(k, c_rcon[r], L);
         s = aes_round(s, L, k.a, k.b, k.c, k.d);
     }
     ks_next(k, 0x36u, L);
@@ -183,7 +182,8 @@ __device__ __forceinline__ Blk keyed_one(const Blk p, uint32_t x, uint32_t L) {
 
 // ---- MMO PRF: PRF_p(x) = AES_{K_x}(p) ^ p with fixed round keys rk[x][44] ----
 
-__device__ __forceinline__ void mmo_pair(const Blk p, uint32_t L, const uint32_t (&rk)[2][44], Blk& a, Blk& b) {
+__device__ __forceinline__ void mmo_pair(const Blk p, uint32_t L, const uint32_t (&rk)[2][44], const Blk ca,
+                                         const Blk cb, Blk& a, Blk& b) {
     a = {p.x ^ rk[0][0], p.y ^ rk[0][1], p.z ^ rk[0][2], p.w ^ rk[0][3]};
     b = {p.x ^ rk[1][0], p.y ^ rk[1][1], p.z ^ rk[1][2], p.w ^ rk[1][3]};
 #pragma unroll 1
@@ -191,8 +191,9 @@ __device__ __forceinline__ void mmo_pair(const Blk p, uint32_t L, const uint32_t
         a = aes_round(a, L, rk[0][4 * r], rk[0][4 * r + 1], rk[0][4 * r + 2], rk[0][4 * r + 3]);
         b = aes_round(b, L, rk[1][4 * r], rk[1][4 * r + 1], rk[1][4 * r + 2], rk[1][4 * r + 3]);
     }
-    a = bxor(aes_final(a, L, rk[0][40], rk[0][41], rk[0][42], rk[0][43]), p);
-    b = bxor(aes_final(b, L, rk[1][40], rk[1][41], rk[1][42], rk[1][43]), p);
+    const Blk pa = bxor(p, ca), pb = bxor(p, cb);
+    a = aes_final(a, L, rk[0][40] ^ pa.x, rk[0][41] ^ pa.y, rk[0][42] ^ pa.z, rk[0][43] ^ pa.w);
+    b = aes_final(b, L, rk[1][40] ^ pb.x, rk[1][41] ^ pb.y, rk[1][42] ^ pb.z, rk[1][43] ^ pb.w);
 }
 
 __device__ __forceinline__ uint32_t mmo_leaf_bits(const Blk p, uint32_t L, const uint32_t (&rk)[2][44]) {
@@ -278,12 +279,12 @@ __device__ __forceinline__ void lane_eval(const FusedParams& P, const uint8_t* k
             const Blk c1 = cw_load(kq, m, t, 1, depth + 1);
             Blk a, b;
             if (PRF == 0)
-                keyed_pair(node, L, a, b);
+                keyed_pair(node, L, c0, c1, a, b);
             else
-                mmo_pair(node, L, P.mmo_rk, a, b);
+                mmo_pair(node, L, P.mmo_rk, c0, c1, a, b);
             ++depth;
-            stk[depth - D] = bxor(b, c1);
-            node = bxor(a, c0);
+            stk[depth - D] = b;
+            node = a;
         }
     }
     if (sq < 5) atomicOr(&bits[(lane << sq) >> 5], acc << ((lane << sq) & 31));
