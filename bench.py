@@ -413,6 +413,18 @@ def main():
     peak = aes_peak_gaes(sms, mhz)
     scan_bytes = sum(min(N, 1 << m) * B for bt in batches for m in bt["ms"])
 
+    # AES engine alone (same device code, no tree walk / scan): the ceiling the fused kernel
+    # approaches; its lookup rate shows how close the engine runs to the shared-memory port
+    rs = np.random.default_rng(7)
+    n_cal = sms * 512
+    _, cal_ms = impir.impir_aes_calibrate(impir.IMPIR_PRF_AES_KEYED, 2000,
+                                          rs.integers(0, 256, (n_cal, 16), dtype=np.uint8), 512)
+    engine_gaes = 2 * 2000 * n_cal / (cal_ms / 1e3) / 1e9
+    engine = {"gaes_per_s": engine_gaes,
+              "lookups_per_clk_per_sm": engine_gaes * 1e9 * 172.5 / (sms * mhz * 1e6),
+              "fused_over_engine": (achieved / engine_gaes) if achieved else None,
+              "note": "keyed node expansions in registers, 172.5 table lookups per block (round 1 shared)"}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -456,6 +468,7 @@ def main():
             "scan": {"logical_gbs": scan_bytes * args.steps / (ms / 1e3) / 1e9, "hbm_peak_gbs": pk.get("hbm_gbs"),
                      "peak_kind": pk_kind},
             "aes_blocks_per_s": blocks_per_step * args.steps / (ms / 1e3),
+            "aes_engine": engine,
             "one_query_per_launch": plain,
             "parity": {"reconstructed_ok": nq - bad, "queries": nq},
             "cpu_baseline": cpu,

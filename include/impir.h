@@ -245,6 +245,15 @@ impir_status impir_answer_noalloc(const void* d_records, uint64_t n_records, uin
 impir_status impir_timing_enable(int enable);
 impir_status impir_timing_read(double* fused_ms, uint64_t* fused_launches, uint64_t* all_launches);
 
+/* AES-only calibration (measurement support; the paper has no counterpart): runs the fused
+ * kernel's PRF engine with nothing around it. Each of n_threads threads (threads_per_cta per
+ * CTA, a multiple of 32, <= 512) starts from its 16-byte seed in `seeds` (host) and applies
+ * iters times p <- PRF_p(0) XOR PRF_p(1) with the given prf; the final states go to `out`
+ * (host, n_threads * 16 bytes) and *ms receives the device time of the timed launch
+ * (2 * iters * n_threads AES-128 blocks). Allocates and frees its own device buffers. */
+impir_status impir_aes_calibrate(int prf, uint32_t iters, uint32_t n_threads, uint32_t threads_per_cta,
+                                 const uint8_t* seeds, uint8_t* out, double* ms);
+
 /* Number of streaming multiprocessors of the current device (0 if none). */
 int32_t impir_device_sm_count(void);
 

@@ -31,6 +31,7 @@ EXPORTS = [
     "impir_set_config", "impir_autotune", "dpf_gen", "impir_reconstruct", "impir_last_error",
     "impir_device_sm_count", "impir_timing_enable", "impir_timing_read", "impir_answer_noalloc",
     "impir_server_create", "impir_server_submit", "impir_server_take", "impir_server_stats", "impir_server_destroy",
+    "impir_aes_calibrate",
 ]
 
 
@@ -91,6 +92,8 @@ def lib():
                 "impir_last_error": (ctypes.c_char_p, []),
                 "impir_device_sm_count": (ctypes.c_int32, []),
                 "impir_timing_enable": (ctypes.c_int, [ctypes.c_int]),
+                "impir_aes_calibrate": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                                       u8p, u8p, ctypes.POINTER(ctypes.c_double)]),
                 "impir_server_create": (ctypes.c_int, [ctypes.POINTER(impir_server_config), ctypes.POINTER(ctypes.c_void_p)]),
                 "impir_server_submit": (ctypes.c_int, [vp, ctypes.c_int32, u8p, ctypes.c_uint64]),
                 "impir_server_take": (ctypes.c_int, [vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
@@ -293,6 +296,16 @@ def impir_answer_noalloc(d_records, n_records: int, record_bytes: int, stride_by
     _check(lib().impir_answer_noalloc(_dev(d_records), n_records, record_bytes, stride_bytes, _dev(d_keys),
                                       _dev(d_key_offsets), n_queries, _dev(d_out), _stream(stream)),
            "impir_answer_noalloc")
+
+
+def impir_aes_calibrate(prf: int, iters: int, seeds: np.ndarray, threads_per_cta: int = 512):
+    """AES-only engine run: returns (final states (n, 16) uint8, device ms)."""
+    sd = np.ascontiguousarray(seeds, dtype=np.uint8).reshape(-1, 16)
+    out = np.zeros_like(sd)
+    ms = ctypes.c_double()
+    _check(lib().impir_aes_calibrate(prf, iters, sd.shape[0], threads_per_cta, ctypes.c_void_p(sd.ctypes.data),
+                                     ctypes.c_void_p(out.ctypes.data), ctypes.byref(ms)), "impir_aes_calibrate")
+    return out, ms.value
 
 
 def impir_timing_enable(enable: bool = True) -> None:
