@@ -157,6 +157,14 @@ def pins(lib):
         if o[0] != int(g[r][0], 2):
             failed.append("fig2")
             break
+    # dpXOR special cases: a unit selection returns exactly that record, none returns zero
+    dbs = rng.integers(0, 256, (9, 5), dtype=np.uint8)
+    for sel, want in ((np.eye(9, dtype=np.uint8)[4], dbs[4]), (np.zeros(9, np.uint8), np.zeros(5, np.uint8))):
+        o = np.zeros(5, np.uint8)
+        lib.orc_dpxor(P(dbs), 9, 5, P(np.ascontiguousarray(sel)), P(o))
+        if not np.array_equal(o, want):
+            failed.append("dpxor_special")
+            break
     # reconstruction and the threaded split on a small DB
     N, B, m = 300, 7, 9
     dbr = rng.integers(0, 256, (N, B), dtype=np.uint8)
