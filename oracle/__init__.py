@@ -55,6 +55,7 @@ def _load():
             lib.orc_dpxor.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint32, u8p, u8p]
             lib.orc_dpxor.restype = None
             lib.orc_answer.argtypes = [u8p, u8p, ctypes.c_uint64, ctypes.c_uint32, u8p]
+            lib.orc_answer_points.argtypes = [u8p, u8p, ctypes.c_uint64, ctypes.c_uint32, u8p]
             lib.orc_answer_threads.argtypes = [u8p, u8p, ctypes.c_uint64, ctypes.c_uint32, u8p, ctypes.c_int]
             lib.orc_gen.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, u8p, u8p, u8p]
             lib.orc_reconstruct.argtypes = [u8p, u8p, ctypes.c_uint32, u8p]
@@ -159,6 +160,15 @@ def answer(key, db: np.ndarray, n_records: int, record_bytes: int, threads: int 
             _load().orc_answer_threads(_ptr(k), _ptr(d), n_records, record_bytes, _ptr(out), threads),
             "answer_threads",
         )
+    return out.tobytes()
+
+
+def answer_points(key, db: np.ndarray, n_records: int, record_bytes: int) -> bytes:
+    """Same answer, every record's leaf from its own root-to-leaf walk (any domain size)."""
+    k = _u8(key)
+    d = np.ascontiguousarray(db, dtype=np.uint8).reshape(-1)
+    out = np.zeros(record_bytes, np.uint8)
+    _check(_load().orc_answer_points(_ptr(k), _ptr(d), n_records, record_bytes, _ptr(out)), "answer_points")
     return out.tobytes()
 
 

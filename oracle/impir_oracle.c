@@ -358,6 +358,28 @@ int orc_answer(const uint8_t* key, const uint8_t* db, uint64_t N, uint32_t recor
     return rc;
 }
 
+/* One server's answer with every leaf evaluated on its own root-to-leaf walk (the
+ * branch-parallel reading of §3.2): for any domain size, cost m AES per record covered. */
+int orc_answer_points(const uint8_t* key, const uint8_t* db, uint64_t N, uint32_t record_bytes, uint8_t* out) {
+    orc_key k;
+    int rc = parse_key(key, &k);
+    if (rc) return rc;
+    if (record_bytes == 0 || N == 0) return ORC_EINVAL;
+    ensure_sbox();
+    uint64_t dom = k.m >= 64 ? UINT64_MAX : ((uint64_t)1 << k.m);
+    uint64_t n = N < dom ? N : dom;
+    memset(out, 0, record_bytes);
+    for (uint64_t j = 0; j < n; j++) {
+        uint8_t leaf[16];
+        node_value(&k, k.m, j, leaf);
+        if (leaf[0] & 1) {
+            const uint8_t* rec = db + j * (uint64_t)record_bytes;
+            for (uint32_t b = 0; b < record_bytes; b++) out[b] ^= rec[b];
+        }
+    }
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------------------
  * Threaded answer: the paper's subtree split (§3.2) + two-stage reduction (§3.3)
  * ---------------------------------------------------------------------------------- */

@@ -153,3 +153,23 @@ def test_empty_batch_and_single_record(built, orc):
         assert r0[0].tobytes() == orc.answer(k0, db, 1, 5)
     finally:
         impir.impir_db_free(dbh)
+
+
+@pytest.mark.parametrize("prf", [0, 1])
+def test_large_domains_over_small_database(built, orc, prf):
+    """Domains of 2^27..2^40 leaves over a 5000-record DB: only the prefix min(2^m, N) counts."""
+    N, B = 5000, 40
+    db = workloads.make_db(N, B, seed=4040)
+    rng = np.random.default_rng(400 + prf)
+    keys = [random_key(rng, m, prf) for m in (27, 33, 40, 40)]
+    pairs = [impir.dpf_gen(a, 40, prf, rng.integers(0, 256, 32, dtype=np.uint8).tobytes()) for a in (0, 4999)]
+    dbh = impir.impir_db_load(db, N, B)
+    try:
+        got = gpu_answers(dbh, keys + [p[0] for p in pairs], B)
+        for i, k in enumerate(keys + [p[0] for p in pairs]):
+            assert got[i].tobytes() == orc.answer_points(k, db, N, B), i
+        other = gpu_answers(dbh, [p[1] for p in pairs], B)
+        assert bytes(got[4] ^ other[0]) == db[0].tobytes()
+        assert bytes(got[5] ^ other[1]) == db[4999].tobytes()
+    finally:
+        impir.impir_db_free(dbh)

@@ -77,3 +77,18 @@ def test_threaded_subtree_split_matches(orc, threads):
         k0, _ = orc.gen(int(rng.integers(0, min(N, 1 << m))), m, 1 if B == 5 else 0,
                         rng.integers(0, 256, 32, dtype=np.uint8).tobytes())
         assert orc.answer(k0, db, N, B, threads=threads) == orc.answer(k0, db, N, B)
+
+
+@pytest.mark.parametrize("prf", [0, 1])
+def test_pointwise_answer_matches_level_by_level(orc, prf):
+    """The branch-parallel answer equals the level-by-level one (and works for m = 40)."""
+    rng = np.random.default_rng(40 + prf)
+    for m, N, B in ((10, 1000, 9), (12, 3000, 16), (8, 100, 3)):
+        db = workloads.make_db(N, B, seed=m)
+        k0, k1 = orc.gen(int(rng.integers(0, min(N, 1 << m))), m, prf, rng.integers(0, 256, 32, dtype=np.uint8).tobytes())
+        assert orc.answer_points(k0, db, N, B) == orc.answer(k0, db, N, B)
+    N, B, m, a = 200, 8, 40, 123
+    db = workloads.make_db(N, B, seed=7)
+    k0, k1 = orc.gen(a, m, prf, bytes(range(32)))
+    r0, r1 = orc.answer_points(k0, db, N, B), orc.answer_points(k1, db, N, B)
+    assert orc.reconstruct(r0, r1) == db[a].tobytes()
