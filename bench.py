@@ -217,7 +217,7 @@ def run_serving(args, impir, workloads):
                                        accumulator_budget=4 * 256 * 512)
     points = []
     try:
-        for rate in workloads.SERVING_RATES:
+        for rate, with_updates in [(r, False) for r in workloads.SERVING_RATES] + [(20_000, True)]:
             arr = workloads.poisson_arrivals(rate, args.serving_requests, dbs=workloads.SERVING_DBS)
             keys = []
             for i in range(len(arr.t)):
@@ -242,24 +242,45 @@ def run_serving(args, impir, workloads):
                     impir.impir_server_submit(server, dbs[int(arr.db[i])][0], k, i)
 
             th = threading.Thread(target=client)
+            upd = {"count": 0, "bytes": 0}
+
+            def updater():
+                # bulk updates of 16 MiB into the largest DB while requests are served
+                urng = np.random.default_rng(rate)
+                h, _, n, b = dbs[-1]
+                rec = urng.integers(0, 256, ((16 << 20) // b, b), dtype=np.uint8)
+                for _ in range(8):
+                    time.sleep(float(arr.t[-1]) / 9)
+                    impir.impir_server_update(server, h, int(urng.integers(0, n - rec.shape[0])), rec)
+                    upd["count"] += 1
+                    upd["bytes"] += rec.nbytes
+
+            tu = threading.Thread(target=updater) if with_updates else None
             t_start = time.perf_counter()
             th.start()
+            if tu:
+                tu.start()
             while len(done) < len(keys):
                 r = impir.impir_server_take(server, 2_000_000)
                 if r is None:
                     break
                 done[r["tag"]] = (r, time.perf_counter())
             th.join()
+            if tu:
+                tu.join()
             t_end = max(t for _, t in done.values())
             after = impir.impir_server_stats(server)
             lat = np.array([r["latency_ns"] for r, _ in done.values()]) / 1e6
             bad = checked = 0
-            for i in range(0, len(keys), max(1, len(keys) // 24)):
+            # with updates interleaved the answers span several DB versions (the version
+            # check is the updates test's job); without, compare a sample with answers alone
+            for i in range(0, len(keys), max(1, len(keys) // 24)) if not with_updates else ():
                 checked += 1
                 h, _, _, b = dbs[int(arr.db[i])]
                 bad += int(done[i][0]["answer"] != impir.impir_answer(h, keys[i], 1, b)[0].tobytes())
             points.append({
                 "offered_req_s": rate, "requests": len(keys), "completed": len(done),
+                "bulk_updates": upd if with_updates else None,
                 "submit_rate_req_s": len(keys) / max(1e-9, t_sub[-1] - t_sub[0]),
                 "queries_per_s": len(done) / (t_end - t_start),
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
@@ -444,6 +465,15 @@ def main():
                "sample": f"{len(qs)} queries of the workload (m={[batches[b]['ms'][i] for b, i in qs]}), "
                          f"threaded oracle, {dt:.1f} s", "bit_identical_to_gpu": bool(agree)}
 
+    # bulk update bandwidth: 256 MiB of new records into the resident DB (synchronous call)
+    upd_n = (256 << 20) // B
+    upd_rec = np.random.default_rng(11).integers(0, 256, (upd_n, B), dtype=np.uint8)
+    t0 = time.perf_counter()
+    impir.impir_db_update(dbh, 12345, upd_rec)
+    upd_s = time.perf_counter() - t0
+    db_update = {"bytes": int(upd_rec.nbytes), "seconds": upd_s, "gb_per_s": upd_rec.nbytes / upd_s / 1e9,
+                 "version": impir.impir_db_version(dbh)}
+
     serving = None
     if rank == 0 and not args.no_serving:
         serving = run_serving(args, impir, workloads)
@@ -473,6 +503,7 @@ def main():
             "parity": {"reconstructed_ok": nq - bad, "queries": nq},
             "cpu_baseline": cpu,
             "serving": serving,
+            "db_update": db_update,
             "setup_s": setup_s,
         }
         print(json.dumps(out), flush=True)

@@ -81,6 +81,21 @@ impir_status impir_db_free(int32_t db_handle);
 impir_status impir_db_info(int32_t db_handle, uint64_t* n_records, uint32_t* record_bytes, uint32_t* stride_bytes,
                            const void** d_records);
 
+/* ---- Bulk updates (§3.3: a stable version answers queries while bulk updates are applied
+ * in windows when the database is idle) ----
+ * Records [first_record, first_record + n_records) are replaced by n_records records of
+ * record_bytes each from host memory `records` (row-major). Every update increments the
+ * database's version (0 after loading). impir_db_update waits for all work on the device to
+ * finish, copies, and returns when later answers will see the new records. The _async form
+ * only enqueues the copy on `cuda_stream` and bumps the version: the caller must order it
+ * after the answers that should see the old records and before those that should see the
+ * new ones, and keep `records` valid until the copy completes. EINVAL: unknown handle or a
+ * range beyond the database. */
+impir_status impir_db_update(int32_t db_handle, uint64_t first_record, uint64_t n_records, const void* records);
+impir_status impir_db_update_async(int32_t db_handle, uint64_t first_record, uint64_t n_records, const void* records,
+                                   void* cuda_stream, uint64_t* new_version);
+impir_status impir_db_version(int32_t db_handle, uint64_t* version);
+
 /* ---- Answering (Algorithm 1: EvaluateDPF + TaskletXOR + MasterXOR + Aggregate) ---- */
 
 /* Answers n_queries keys against one database: for each key k,
@@ -178,12 +193,21 @@ impir_status impir_server_submit(impir_server* server, int32_t db_handle, const 
 
 /* Waits up to timeout_us for any finished request and returns it: its tag, database, answer
  * (copied into `answer`, record_bytes of its database, at most answer_capacity), the latency
- * from submit to completion in nanoseconds, and the size of the batch it ran in.
+ * from submit to completion in nanoseconds, the size of the batch it ran in, and the version
+ * of the database the answer was computed on (see impir_db_update).
  * ETIMEOUT: nothing finished in time. A request that failed returns its failure status
  * (with its tag filled in). */
 impir_status impir_server_take(impir_server* server, uint32_t timeout_us, uint64_t* tag, int32_t* db_handle,
                                uint8_t* answer, uint32_t answer_capacity, uint32_t* answer_bytes,
-                               uint64_t* latency_ns, uint32_t* batch_size);
+                               uint64_t* latency_ns, uint32_t* batch_size, uint64_t* db_version);
+
+/* Queues a bulk update of records [first_record, first_record + n_records) of a database
+ * (host `records`, copied before return). The dispatcher applies queued updates in order, each
+ * as soon as no batch on its database is in flight; requests for that database wait until it
+ * is applied, so every answer is computed on one whole version. EINVAL: unknown database or a
+ * range beyond it. */
+impir_status impir_server_update(impir_server* server, int32_t db_handle, uint64_t first_record, uint64_t n_records,
+                                 const void* records);
 
 /* Counters: batches launched, queries launched, most batches in flight at once, requests
  * still waiting for admission. */

@@ -31,7 +31,7 @@ EXPORTS = [
     "impir_set_config", "impir_autotune", "dpf_gen", "impir_reconstruct", "impir_last_error",
     "impir_device_sm_count", "impir_timing_enable", "impir_timing_read", "impir_answer_noalloc",
     "impir_server_create", "impir_server_submit", "impir_server_take", "impir_server_stats", "impir_server_destroy",
-    "impir_aes_calibrate",
+    "impir_aes_calibrate", "impir_db_update", "impir_db_update_async", "impir_db_version", "impir_server_update",
 ]
 
 
@@ -99,7 +99,12 @@ def lib():
                 "impir_server_take": (ctypes.c_int, [vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
                                                      ctypes.POINTER(ctypes.c_int32), u8p, ctypes.c_uint32,
                                                      ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64),
-                                                     ctypes.POINTER(ctypes.c_uint32)]),
+                                                     ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64)]),
+                "impir_server_update": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, vp]),
+                "impir_db_update": (ctypes.c_int, [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, vp]),
+                "impir_db_update_async": (ctypes.c_int, [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, vp, vp,
+                                                         ctypes.POINTER(ctypes.c_uint64)]),
+                "impir_db_version": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]),
                 "impir_server_stats": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                                       ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
                 "impir_server_destroy": (ctypes.c_int, [vp]),
@@ -268,15 +273,35 @@ def impir_server_submit(server: int, db: int, key: bytes, tag: int) -> None:
 def impir_server_take(server: int, timeout_us: int, answer_capacity: int = 1 << 16):
     """Next finished request: dict(tag, db, answer, latency_ns, batch) or None on timeout."""
     tag, db, nb, lat, bs = ctypes.c_uint64(), ctypes.c_int32(), ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_uint32()
+    ver = ctypes.c_uint64()
     buf = np.zeros(answer_capacity, np.uint8)
     st = lib().impir_server_take(ctypes.c_void_p(server), timeout_us, ctypes.byref(tag), ctypes.byref(db),
                                  ctypes.c_void_p(buf.ctypes.data), answer_capacity, ctypes.byref(nb),
-                                 ctypes.byref(lat), ctypes.byref(bs))
+                                 ctypes.byref(lat), ctypes.byref(bs), ctypes.byref(ver))
     if st == IMPIR_ETIMEOUT:
         return None
     _check(st, "impir_server_take")
     return {"tag": tag.value, "db": db.value, "answer": buf[: nb.value].tobytes(), "latency_ns": lat.value,
-            "batch": bs.value}
+            "batch": bs.value, "version": ver.value}
+
+
+def impir_server_update(server: int, db: int, first_record: int, records: np.ndarray) -> None:
+    """Queue a bulk update of len(records) records starting at first_record."""
+    r = np.ascontiguousarray(records, dtype=np.uint8)
+    n = r.shape[0] if r.ndim == 2 else 0
+    _check(lib().impir_server_update(ctypes.c_void_p(server), db, first_record, n, ctypes.c_void_p(r.ctypes.data)),
+           "impir_server_update")
+
+
+def impir_db_update(db: int, first_record: int, records: np.ndarray) -> None:
+    r = np.ascontiguousarray(records, dtype=np.uint8)
+    _check(lib().impir_db_update(db, first_record, r.shape[0], ctypes.c_void_p(r.ctypes.data)), "impir_db_update")
+
+
+def impir_db_version(db: int) -> int:
+    v = ctypes.c_uint64()
+    _check(lib().impir_db_version(db, ctypes.byref(v)), "impir_db_version")
+    return v.value
 
 
 def impir_server_stats(server: int) -> dict:

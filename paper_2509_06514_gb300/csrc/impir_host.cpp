@@ -98,6 +98,7 @@ struct Db {
     bool live = false;
     bool cfg_set = false;
     impir_config cfg{};
+    uint64_t version = 0;  // bumped by every bulk update
 };
 
 std::mutex g_db_mu;
@@ -442,6 +443,40 @@ impir_status impir_db_info(int32_t h, uint64_t* n, uint32_t* bytes, uint32_t* st
     if (bytes) *bytes = db.bytes;
     if (stride) *stride = db.stride;
     if (d) *d = db.d;
+    return IMPIR_OK;
+}
+
+impir_status impir_db_version(int32_t h, uint64_t* version) {
+    Db db;
+    if (impir_status s = get_db(h, &db)) return s;
+    if (version) *version = db.version;
+    return IMPIR_OK;
+}
+
+impir_status impir_db_update_async(int32_t h, uint64_t first, uint64_t n, const void* records, void* stream,
+                                   uint64_t* new_version) {
+    if (!records && n) return fail(IMPIR_EINVAL, "NULL records");
+    std::lock_guard<std::mutex> lk(g_db_mu);
+    if (h < 1 || size_t(h) > g_dbs.size() || !g_dbs[h - 1].live) return fail(IMPIR_EINVAL, "unknown database handle %d", h);
+    Db& db = g_dbs[h - 1];
+    if (first > db.n || n > db.n - first) return fail(IMPIR_EINVAL, "update range beyond the database");
+    if (n) {
+        uint8_t* dst = static_cast<uint8_t*>(const_cast<void*>(db.d)) + first * db.stride;
+        CK(cudaMemcpy2DAsync(dst, db.stride, records, db.bytes, db.bytes, n, cudaMemcpyHostToDevice,
+                             static_cast<cudaStream_t>(stream)),
+           "database update copy");
+    }
+    db.version += 1;
+    if (new_version) *new_version = db.version;
+    return IMPIR_OK;
+}
+
+impir_status impir_db_update(int32_t h, uint64_t first, uint64_t n, const void* records) {
+    DeviceState* dev;
+    if (impir_status s = need_device(&dev)) return s;
+    CK(cudaDeviceSynchronize(), "wait for answers in flight");
+    if (impir_status s = impir_db_update_async(h, first, n, records, nullptr, nullptr)) return s;
+    CK(cudaDeviceSynchronize(), "database update");
     return IMPIR_OK;
 }
 

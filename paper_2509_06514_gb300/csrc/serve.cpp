@@ -15,6 +15,8 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
+#include <set>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -46,6 +48,14 @@ struct Done {
     std::vector<uint8_t> answer;
     uint64_t latency_ns;
     uint32_t batch;
+    uint64_t version;
+};
+
+// A bulk update waiting for an idle window of its database.
+struct Update {
+    int32_t db;
+    uint64_t first, n;
+    std::vector<uint8_t> records;
 };
 
 struct Slot {
@@ -62,6 +72,8 @@ struct Slot {
     std::vector<Request> reqs;
     uint32_t record_bytes = 0;
     uint64_t acc_bytes = 0;
+    int32_t db = 0;
+    uint64_t version = 0;
 };
 
 size_t max_key_bytes() { return impir_key_bytes(IMPIR_MAX_DOMAIN_BITS); }
@@ -75,6 +87,10 @@ struct impir_server {
     std::condition_variable cv_work, cv_done;
     std::deque<Request> pending;
     std::deque<Done> done;
+    std::deque<Update> updates;
+    std::map<int32_t, uint32_t> inflight_per_db;
+    cudaStream_t upd_stream = nullptr;
+    uint64_t updates_applied = 0;
     std::vector<Slot> slots;
     uint64_t inflight_acc = 0;
     uint64_t batches = 0, queries = 0;
@@ -112,29 +128,52 @@ void harvest(impir_server* S) {
             d.answer.assign(s.h_out + i * s.record_bytes, s.h_out + (i + 1) * s.record_bytes);
             d.latency_ns = uint64_t(std::chrono::duration_cast<std::chrono::nanoseconds>(now - s.reqs[i].t_submit).count());
             d.batch = uint32_t(s.reqs.size());
+            d.version = s.version;
             S->done.push_back(std::move(d));
         }
         S->inflight_acc -= s.acc_bytes;
         S->inflight_batches -= 1;
+        S->inflight_per_db[s.db] -= 1;
         s.reqs.clear();
         s.busy = false;
         S->cv_done.notify_all();
     }
 }
 
+// Applies queued bulk updates, oldest first, as long as their database has no batch in
+// flight (lock held). The copy completes before any later batch on that database launches.
+void apply_updates(impir_server* S) {
+    while (!S->updates.empty()) {
+        Update& u = S->updates.front();
+        if (S->inflight_per_db[u.db] > 0) break;
+        uint64_t v = 0;
+        if (impir_db_update_async(u.db, u.first, u.n, u.records.data(), S->upd_stream, &v) == IMPIR_OK)
+            cudaStreamSynchronize(S->upd_stream);
+        S->updates.pop_front();
+        S->updates_applied += 1;
+    }
+}
+
 // Admits and launches as many batches as free slots and the budget allow (lock held).
+// Requests for a database with a pending update wait until the update is applied.
 void launch_ready(impir_server* S) {
+    std::set<int32_t> blocked;
+    for (const Update& u : S->updates) blocked.insert(u.db);
     for (Slot& s : S->slots) {
         if (s.busy || S->pending.empty()) continue;
-        const int32_t db = S->pending.front().db;
+        auto first = S->pending.begin();
+        while (first != S->pending.end() && blocked.count(first->db)) ++first;
+        if (first == S->pending.end()) break;
+        const int32_t db = first->db;
         uint64_t n_records = 0;
         uint32_t rb = 0, stride = 0;
         const void* dptr = nullptr;
-        if (impir_db_info(db, &n_records, &rb, &stride, &dptr) != IMPIR_OK) {
+        uint64_t version = 0;
+        if (impir_db_info(db, &n_records, &rb, &stride, &dptr) != IMPIR_OK || impir_db_version(db, &version) != IMPIR_OK) {
             // the database went away: fail that request
-            Request r = std::move(S->pending.front());
-            S->pending.pop_front();
-            Done d{r.tag, r.db, IMPIR_EINVAL, {}, 0, 0};
+            Request r = std::move(*first);
+            S->pending.erase(first);
+            Done d{r.tag, r.db, IMPIR_EINVAL, {}, 0, 0, 0};
             S->done.push_back(std::move(d));
             S->cv_done.notify_all();
             continue;
@@ -145,7 +184,7 @@ void launch_ready(impir_server* S) {
         if (cap == 0) break;  // wait for in-flight batches to release accumulator memory
         // oldest request first, then later ones for the same database, in arrival order
         std::vector<Request> take;
-        for (auto it = S->pending.begin(); it != S->pending.end() && take.size() < cap;) {
+        for (auto it = first; it != S->pending.end() && take.size() < cap;) {
             if (it->db == db) {
                 take.push_back(std::move(*it));
                 it = S->pending.erase(it);
@@ -170,7 +209,7 @@ void launch_ready(impir_server* S) {
         if (st == IMPIR_OK && e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
         if (st != IMPIR_OK || e != cudaSuccess) {
             for (Request& r : take) {
-                Done d{r.tag, r.db, st != IMPIR_OK ? st : IMPIR_ECUDA, {}, 0, n};
+                Done d{r.tag, r.db, st != IMPIR_OK ? st : IMPIR_ECUDA, {}, 0, n, version};
                 S->done.push_back(std::move(d));
             }
             S->cv_done.notify_all();
@@ -179,6 +218,9 @@ void launch_ready(impir_server* S) {
         s.reqs = std::move(take);
         s.record_bytes = rb;
         s.acc_bytes = uint64_t(n) * stride;
+        s.db = db;
+        s.version = version;
+        S->inflight_per_db[db] += 1;
         s.busy = true;
         S->inflight_acc += s.acc_bytes;
         S->inflight_batches += 1;
@@ -193,12 +235,13 @@ void dispatcher(impir_server* S) {
     std::unique_lock<std::mutex> lk(S->mu);
     while (!S->stop.load()) {
         harvest(S);
+        apply_updates(S);
         launch_ready(S);
         const bool any_busy = S->inflight_batches > 0;
         if (any_busy) {
             // short host-side poll interval while batches run
             S->cv_work.wait_for(lk, std::chrono::microseconds(20));
-        } else if (S->pending.empty()) {
+        } else if (S->pending.empty() && S->updates.empty()) {
             S->cv_work.wait_for(lk, std::chrono::milliseconds(2));
         }
     }
@@ -239,6 +282,11 @@ impir_status impir_server_create(const impir_server_config* cfg, impir_server** 
             return set_error(IMPIR_ENOMEM, "server buffers could not be allocated");
         }
     }
+    if (cudaStreamCreateWithFlags(&S->upd_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        for (Slot& t : S->slots) free_slot(t);
+        delete S;
+        return set_error(IMPIR_ENOMEM, "server update stream could not be created");
+    }
     S->th = std::thread(dispatcher, S);
     *out = S;
     return IMPIR_OK;
@@ -269,7 +317,7 @@ impir_status impir_server_submit(impir_server* S, int32_t db, const uint8_t* key
 
 impir_status impir_server_take(impir_server* S, uint32_t timeout_us, uint64_t* tag, int32_t* db, uint8_t* answer,
                                uint32_t answer_capacity, uint32_t* answer_bytes, uint64_t* latency_ns,
-                               uint32_t* batch_size) {
+                               uint32_t* batch_size, uint64_t* db_version) {
     if (!S) return set_error(IMPIR_EINVAL, "NULL server");
     std::unique_lock<std::mutex> lk(S->mu);
     if (!S->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), [S] { return !S->done.empty(); }))
@@ -281,6 +329,7 @@ impir_status impir_server_take(impir_server* S, uint32_t timeout_us, uint64_t* t
     if (db) *db = d.db;
     if (latency_ns) *latency_ns = d.latency_ns;
     if (batch_size) *batch_size = d.batch;
+    if (db_version) *db_version = d.version;
     if (answer_bytes) *answer_bytes = uint32_t(d.answer.size());
     if (d.status != IMPIR_OK) return set_error(d.status, "request failed");
     if (d.answer.size() > answer_capacity) return set_error(IMPIR_EINVAL, "answer buffer too small");
@@ -305,7 +354,29 @@ impir_status impir_server_destroy(impir_server* S) {
     S->cv_work.notify_all();
     if (S->th.joinable()) S->th.join();
     for (Slot& s : S->slots) free_slot(s);
+    if (S->upd_stream) cudaStreamDestroy(S->upd_stream);
     delete S;
+    return IMPIR_OK;
+}
+
+impir_status impir_server_update(impir_server* S, int32_t db, uint64_t first_record, uint64_t n_records,
+                                 const void* records) {
+    if (!S || (!records && n_records)) return set_error(IMPIR_EINVAL, "NULL argument");
+    uint64_t n = 0;
+    uint32_t rb = 0;
+    if (impir_db_info(db, &n, &rb, nullptr, nullptr) != IMPIR_OK) return set_error(IMPIR_EINVAL, "unknown database");
+    if (first_record > n || n_records > n - first_record) return set_error(IMPIR_EINVAL, "update range beyond the database");
+    Update u;
+    u.db = db;
+    u.first = first_record;
+    u.n = n_records;
+    const uint8_t* p = static_cast<const uint8_t*>(records);
+    u.records.assign(p, p + n_records * rb);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->updates.push_back(std::move(u));
+    }
+    S->cv_work.notify_one();
     return IMPIR_OK;
 }
 
