@@ -47,6 +47,7 @@ def parse_args():
                    help="fixed launch shape lane_bits,queries_per_warp,warps_per_cta (skips autotuning)")
     p.add_argument("--cpu-sample", type=int, default=2, help="queries in the oracle's timed sample")
     p.add_argument("--no-serving", action="store_true", help="skip the serving sweep (three resident DBs)")
+    p.add_argument("--no-streamed", action="store_true", help="skip the host-streamed database measurement")
     p.add_argument("--serving-requests", type=int, default=2000, help="requests per arrival rate")
     return p.parse_args()
 
@@ -465,6 +466,38 @@ def main():
                "sample": f"{len(qs)} queries of the workload (m={[batches[b]['ms'][i] for b, i in qs]}), "
                          f"threaded oracle, {dt:.1f} s", "bit_identical_to_gpu": bool(agree)}
 
+    # database streamed from host memory (the larger-than-HBM path): the largest batch against
+    # the 8 GiB DB in 1 GiB chunks from pinned host memory, vs the same batch resident
+    streamed = None
+    if rank == 0 and not args.no_streamed:
+        big = max(batches, key=lambda bt: bt["n"])
+        rt = torch.cuda.cudart()
+        reg = rt.cudaHostRegister(db.ctypes.data, db.nbytes, 0)
+        try:
+            t0 = time.perf_counter()
+            res = impir.impir_answer(dbh, big["blob0"], big["n"], B)
+            t_res = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            got, scfg = impir.impir_answer_streamed(db, N, B, big["blob0"], big["n"], 1 << 30)
+            t_str = time.perf_counter() - t0
+            dev_buf = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+            host_view = torch.from_numpy(db.reshape(-1)[: 1 << 30])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(4):
+                dev_buf.copy_(host_view, non_blocking=True)
+            torch.cuda.synchronize()
+            link = 4 * (1 << 30) / (time.perf_counter() - t0) / 1e9
+            del dev_buf
+            streamed = {"queries": big["n"], "db_bytes": N * B, "chunk_bytes": 1 << 30, "pinned": int(reg) == 0,
+                        "resident_queries_per_s": big["n"] / t_res, "streamed_queries_per_s": big["n"] / t_str,
+                        "streamed_over_resident": t_res / t_str, "h2d_link_gb_per_s": link,
+                        "db_stream_gb_per_s": N * B / t_str / 1e9, "bit_identical": bool(np.array_equal(got, res)),
+                        "launch": scfg}
+        finally:
+            if int(reg) == 0:
+                rt.cudaHostUnregister(db.ctypes.data)
+
     # bulk update bandwidth: 256 MiB of new records into the resident DB (synchronous call)
     upd_n = (256 << 20) // B
     upd_rec = np.random.default_rng(11).integers(0, 256, (upd_n, B), dtype=np.uint8)
@@ -504,6 +537,7 @@ def main():
             "cpu_baseline": cpu,
             "serving": serving,
             "db_update": db_update,
+            "streamed": streamed,
             "setup_s": setup_s,
         }
         print(json.dumps(out), flush=True)

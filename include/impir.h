@@ -163,6 +163,21 @@ impir_status impir_autotune(int32_t db_handle, const uint8_t* d_keys, const uint
                             uint32_t n_queries, uint8_t* d_out, void* d_workspace, size_t workspace_bytes,
                             void* cuda_stream, impir_config* best);
 
+/* ---- Databases larger than device memory ---- */
+
+/* Database larger than device memory (§3.3: evaluate the linear operations over the DB in
+ * batches of chunks): answers n_queries host keys against n_records records of record_bytes
+ * each that stay in host memory `records`, streaming them through the device in chunks of
+ * about chunk_bytes (rounded to whole warp tiles), two chunk buffers deep, the copy of one
+ * chunk overlapping the fused launch on the previous one; per-query accumulators persist
+ * across chunks. Same answers as impir_answer on the same records. Pinned host memory
+ * (cudaHostAlloc / cudaHostRegister) lets the copies run at full link bandwidth. `out` is
+ * host memory of n_queries * record_bytes bytes; *used (may be NULL) receives the launch
+ * shape. Allocates its buffers for the call and frees them before returning. */
+impir_status impir_answer_streamed(const void* records, uint64_t n_records, uint32_t record_bytes,
+                                   const uint8_t* keys, uint32_t n_queries, uint8_t* out, uint64_t chunk_bytes,
+                                   impir_config* used);
+
 /* ---- Serving: continuous batching over resident databases (§3.4 query batching) ----
  * A server owns `streams` CUDA streams, each with device buffers for one batch of up to
  * max_batch queries. Any thread may submit requests (one key for one registered database,

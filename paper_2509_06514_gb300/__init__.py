@@ -32,6 +32,7 @@ EXPORTS = [
     "impir_device_sm_count", "impir_timing_enable", "impir_timing_read", "impir_answer_noalloc",
     "impir_server_create", "impir_server_submit", "impir_server_take", "impir_server_stats", "impir_server_destroy",
     "impir_aes_calibrate", "impir_db_update", "impir_db_update_async", "impir_db_version", "impir_server_update",
+    "impir_answer_streamed",
 ]
 
 
@@ -105,6 +106,8 @@ def lib():
                 "impir_db_update_async": (ctypes.c_int, [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, vp, vp,
                                                          ctypes.POINTER(ctypes.c_uint64)]),
                 "impir_db_version": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]),
+                "impir_answer_streamed": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint32, u8p, ctypes.c_uint32, u8p,
+                                                         ctypes.c_uint64, ctypes.POINTER(impir_config)]),
                 "impir_server_stats": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                                       ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
                 "impir_server_destroy": (ctypes.c_int, [vp]),
@@ -190,6 +193,22 @@ def impir_answer(db: int, keys, n_queries: int, record_bytes: int) -> np.ndarray
     out = np.zeros((n_queries, record_bytes), np.uint8)
     _check(lib().impir_answer(db, kp, n_queries, ctypes.c_void_p(out.ctypes.data)), "impir_answer")
     return out
+
+
+def impir_answer_streamed(records, n_records: int, record_bytes: int, keys, n_queries: int, chunk_bytes: int):
+    """Answer against a host-resident database streamed through the device in chunks.
+    `records` is a numpy array or an integer host pointer; returns (answers, launch shape)."""
+    if isinstance(records, int):
+        rp = ctypes.c_void_p(records)
+    else:
+        arr, rp = _host(records)
+        assert arr.size >= n_records * record_bytes
+    _, kp = _host(keys)
+    out = np.zeros((n_queries, record_bytes), np.uint8)
+    cfg = impir_config()
+    _check(lib().impir_answer_streamed(rp, n_records, record_bytes, kp, n_queries, ctypes.c_void_p(out.ctypes.data),
+                                       chunk_bytes, ctypes.byref(cfg)), "impir_answer_streamed")
+    return out, cfg.as_dict()
 
 
 def impir_workspace_bytes(n_queries: int, stride_bytes: int) -> int:

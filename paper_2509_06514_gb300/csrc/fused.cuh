@@ -332,7 +332,7 @@ __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_ba
         uint4 acc[QC];
 #pragma unroll
         for (int q = 0; q < QC; ++q) acc[q] = make_uint4(0, 0, 0, 0);
-        const uint4* base = P.db + tile_base * W + lk;
+        const uint4* base = P.db + (tile_base - P.rec_lo) * W + lk;
         for (uint32_t c0 = 0; c0 < nrec; c0 += 32) {
             uint32_t sel[QC];
 #pragma unroll
@@ -390,7 +390,7 @@ __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_ba
 #pragma unroll 2
                 for (uint32_t i = 0; i < nloc; ++i) {
                     uint4 v[NK];
-                    const uint4* rec = P.db + (tile_base + c0 + i) * W;
+                    const uint4* rec = P.db + (tile_base - P.rec_lo + c0 + i) * W;
 #pragma unroll
                     for (int c = 0; c < NK; ++c) {
                         const uint32_t k = k0 + lane + 32 * c;

@@ -615,6 +615,132 @@ impir_status impir_autotune(int32_t h, const uint8_t* d_keys, const uint32_t* d_
     return impir_set_config(h, &best_c);
 }
 
+// ---- databases larger than HBM: streamed in chunks (§3.3) ----
+
+impir_status impir_answer_streamed(const void* records, uint64_t N, uint32_t B, const uint8_t* keys, uint32_t n,
+                                   uint8_t* out, uint64_t chunk_bytes, impir_config* used) {
+    if (!records || !keys || !out) return fail(IMPIR_EINVAL, "NULL argument");
+    if (N == 0 || B == 0 || N > (1ull << IMPIR_MAX_DOMAIN_BITS)) return fail(IMPIR_EINVAL, "bad database size");
+    if (n == 0) return IMPIR_OK;
+    DeviceState* dev;
+    if (impir_status s = need_device(&dev)) return s;
+    std::vector<uint32_t> offs;
+    size_t total = 0;
+    if (impir_status s = parse_host_keys(keys, n, offs, total)) return s;
+    const uint32_t stride = (B + 15u) & ~15u, words = stride / 16;
+    const impir_config cfg = default_config(N, words, n, dev->sms);
+    if (used) *used = cfg;
+    const uint64_t T = 32ull << cfg.lane_bits;  // warp tile: chunks hold whole tiles
+    uint64_t chunk = (chunk_bytes / stride) / T * T;
+    if (chunk < T) chunk = T;
+    if (chunk > N) chunk = (N + T - 1) / T * T;
+    const uint64_t nchunks = (N + chunk - 1) / chunk;
+    const WsLayout lay = ws_layout(n, stride);
+
+    uint8_t *d_keys = nullptr, *d_ws = nullptr, *d_out = nullptr, *d_buf[2] = {nullptr, nullptr};
+    uint32_t* d_off = nullptr;
+    cudaStream_t cs = nullptr, ks = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+    impir_status st = IMPIR_OK;
+    auto cleanup = [&]() {
+        if (cs) cudaStreamSynchronize(cs);
+        if (ks) cudaStreamSynchronize(ks);
+        cudaFree(d_keys);
+        cudaFree(d_off);
+        cudaFree(d_ws);
+        cudaFree(d_out);
+        cudaFree(d_buf[0]);
+        cudaFree(d_buf[1]);
+        for (int i = 0; i < 2; ++i) {
+            if (copied[i]) cudaEventDestroy(copied[i]);
+            if (consumed[i]) cudaEventDestroy(consumed[i]);
+        }
+        if (cs) cudaStreamDestroy(cs);
+        if (ks) cudaStreamDestroy(ks);
+    };
+    cudaError_t e = cudaMalloc(&d_keys, total);
+    if (e == cudaSuccess) e = cudaMalloc(&d_off, size_t(n) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&d_ws, lay.total);
+    if (e == cudaSuccess) e = cudaMalloc(&d_out, size_t(n) * B);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaMalloc(&d_buf[i], chunk * stride);
+        if (e == cudaSuccess) e = cudaMemset(d_buf[i], 0, chunk * stride);  // padding bytes stay zero
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&consumed[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ks, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_keys, keys, total, cudaMemcpyHostToDevice, ks);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, offs.data(), size_t(n) * 4, cudaMemcpyHostToDevice, ks);
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(e == cudaErrorMemoryAllocation ? IMPIR_ENOMEM : IMPIR_ECUDA, "streamed answer setup: %s",
+                    cudaGetErrorString(e));
+    }
+    const uint8_t* src = static_cast<const uint8_t*>(records);
+    for (uint64_t c = 0; c < nchunks && e == cudaSuccess; ++c) {
+        const int b = int(c & 1);
+        const uint64_t lo = c * chunk, cnt = std::min(chunk, N - lo);
+        // copy stream: refill buffer b once the launch two chunks back has read it
+        if (c >= 2) e = cudaStreamWaitEvent(cs, consumed[b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(d_buf[b], stride, src + lo * B, B, B, cnt, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(copied[b], cs);
+        // compute stream: this chunk's warp tiles, accumulating into the same answers
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ks, copied[b], 0);
+        if (e != cudaSuccess) break;
+        SetupParams sp{};
+        sp.keys = d_keys;
+        sp.key_off = d_off;
+        sp.ws = d_ws;
+        sp.lay = lay;
+        sp.n_records = N;
+        sp.n_queries = n;
+        sp.words = words;
+        sp.lane_bits = cfg.lane_bits;
+        sp.qpw = cfg.queries_per_warp;
+        sp.tile_lo = lo / T;
+        sp.tile_hi = (lo + cnt + T - 1) / T;
+        sp.keep_acc = c > 0;
+        e = launch_setup(sp, ks);
+        FusedParams fp{};
+        fp.db = reinterpret_cast<const uint4*>(d_buf[b]);
+        fp.keys = d_keys;
+        fp.key_off = d_off;
+        fp.ws = d_ws;
+        fp.te0 = dev->d_te0;
+        fp.lay = lay;
+        fp.n_records = N;
+        fp.n_queries = n;
+        fp.words = words;
+        fp.lane_bits = cfg.lane_bits;
+        fp.bits_words = 1u << cfg.lane_bits;
+        fp.rec_lo = lo;
+        std::memcpy(fp.mmo_rk, dev->mmo_rk, sizeof fp.mmo_rk);
+        if (e == cudaSuccess)
+            e = launch_fused(cfg.queries_per_warp, nk_for(words), dim3(dev->sms), dim3(cfg.warps_per_cta * 32),
+                             smem_for(cfg), ks, fp);
+        if (e == cudaSuccess) e = cudaEventRecord(consumed[b], ks);
+        count_launches(2);
+    }
+    if (e == cudaSuccess) {
+        FinalizeParams zp{};
+        zp.ws = d_ws;
+        zp.lay = lay;
+        zp.out = d_out;
+        zp.n_queries = n;
+        zp.record_bytes = B;
+        zp.stride = stride;
+        e = launch_finalize(zp, ks);
+        count_launches(1);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, size_t(n) * B, cudaMemcpyDeviceToHost, ks);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ks);
+    if (e != cudaSuccess) st = cuda_fail(e, "streamed answer");
+    cleanup();
+    return st;
+}
+
 // ---- client side ----
 
 impir_status impir_reconstruct(const uint8_t* r0, const uint8_t* r1, uint32_t record_bytes, uint8_t* out) {

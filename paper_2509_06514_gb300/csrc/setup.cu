@@ -85,14 +85,19 @@ __global__ void __launch_bounds__(1024) setup_kernel(const SetupParams S) {
             const unsigned long long tiles = m >= 5 + S.lane_bits ? (n_eff + tbig - 1) / tbig : 1ull;
             if (tiles > prev) {
                 const uint32_t gcum = gstart[m] + ngrp[m];  // groups with domain bits >= m
-                segs[nseg].tile_lo = prev;
-                segs[nseg].unit_lo = unit;
-                segs[nseg].count = gcum;
-                segs[nseg].pad = 0;
-                segs[nseg].pad2 = 0;
-                unit += (tiles - prev) * gcum;
+                // clip to the tiles this launch covers (a chunk of a streamed database)
+                const unsigned long long lo = prev > S.tile_lo ? prev : S.tile_lo;
+                const unsigned long long hi = (S.tile_hi == 0 || tiles < S.tile_hi) ? tiles : S.tile_hi;
+                if (hi > lo) {
+                    segs[nseg].tile_lo = lo;
+                    segs[nseg].unit_lo = unit;
+                    segs[nseg].count = gcum;
+                    segs[nseg].pad = 0;
+                    segs[nseg].pad2 = 0;
+                    unit += (hi - lo) * gcum;
+                    ++nseg;
+                }
                 prev = tiles;
-                ++nseg;
             }
         }
         hdr->counter = 0;
@@ -122,9 +127,11 @@ __global__ void __launch_bounds__(1024) setup_kernel(const SetupParams S) {
         d.pad = 0;
         groups[gi] = d;
     }
-    // 5. zero the accumulators
-    const size_t nacc = size_t(S.n_queries) * S.words;
-    for (size_t i = tid; i < nacc; i += nthr) acc[i] = make_uint4(0, 0, 0, 0);
+    // 5. zero the accumulators (kept across the chunks of a streamed database)
+    if (!S.keep_acc) {
+        const size_t nacc = size_t(S.n_queries) * S.words;
+        for (size_t i = tid; i < nacc; i += nthr) acc[i] = make_uint4(0, 0, 0, 0);
+    }
 }
 
 __global__ void finalize_kernel(const FinalizeParams F) {
