@@ -481,14 +481,15 @@ def main():
             got, scfg = impir.impir_answer_streamed(db, N, B, big["blob0"], big["n"], 1 << 30)
             t_str = time.perf_counter() - t0
             dev_buf = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
-            host_view = torch.from_numpy(db.reshape(-1)[: 1 << 30])
+            host_buf = torch.empty(1 << 30, dtype=torch.uint8, pin_memory=True)
+            dev_buf.copy_(host_buf, non_blocking=True)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for _ in range(4):
-                dev_buf.copy_(host_view, non_blocking=True)
+                dev_buf.copy_(host_buf, non_blocking=True)
             torch.cuda.synchronize()
             link = 4 * (1 << 30) / (time.perf_counter() - t0) / 1e9
-            del dev_buf
+            del dev_buf, host_buf
             streamed = {"queries": big["n"], "db_bytes": N * B, "chunk_bytes": 1 << 30, "pinned": int(reg) == 0,
                         "resident_queries_per_s": big["n"] / t_res, "streamed_queries_per_s": big["n"] / t_str,
                         "streamed_over_resident": t_res / t_str, "h2d_link_gb_per_s": link,

@@ -462,9 +462,14 @@ impir_status impir_db_update_async(int32_t h, uint64_t first, uint64_t n, const 
     if (first > db.n || n > db.n - first) return fail(IMPIR_EINVAL, "update range beyond the database");
     if (n) {
         uint8_t* dst = static_cast<uint8_t*>(const_cast<void*>(db.d)) + first * db.stride;
-        CK(cudaMemcpy2DAsync(dst, db.stride, records, db.bytes, db.bytes, n, cudaMemcpyHostToDevice,
-                             static_cast<cudaStream_t>(stream)),
-           "database update copy");
+        // one contiguous copy when records carry no padding; row-by-row otherwise
+        if (db.stride == db.bytes)
+            CK(cudaMemcpyAsync(dst, records, n * db.bytes, cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream)),
+               "database update copy");
+        else
+            CK(cudaMemcpy2DAsync(dst, db.stride, records, db.bytes, db.bytes, n, cudaMemcpyHostToDevice,
+                                 static_cast<cudaStream_t>(stream)),
+               "database update copy");
     }
     db.version += 1;
     if (new_version) *new_version = db.version;
@@ -684,7 +689,8 @@ impir_status impir_answer_streamed(const void* records, uint64_t N, uint32_t B, 
         // copy stream: refill buffer b once the launch two chunks back has read it
         if (c >= 2) e = cudaStreamWaitEvent(cs, consumed[b], 0);
         if (e == cudaSuccess)
-            e = cudaMemcpy2DAsync(d_buf[b], stride, src + lo * B, B, B, cnt, cudaMemcpyHostToDevice, cs);
+            e = stride == B ? cudaMemcpyAsync(d_buf[b], src + lo * B, cnt * B, cudaMemcpyHostToDevice, cs)
+                            : cudaMemcpy2DAsync(d_buf[b], stride, src + lo * B, B, B, cnt, cudaMemcpyHostToDevice, cs);
         if (e == cudaSuccess) e = cudaEventRecord(copied[b], cs);
         // compute stream: this chunk's warp tiles, accumulating into the same answers
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ks, copied[b], 0);
