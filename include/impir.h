@@ -16,7 +16,9 @@
  *   byte 0   version, must be IMPIR_KEY_VERSION (1)
  *   byte 1   prf, an impir_prf
  *   byte 2   m, the domain bits, 1..IMPIR_MAX_DOMAIN_BITS; the domain is 2^m leaves
- *   bytes 3..7 zero
+ *   byte 3   party index b (0 or 1): which server the key is for; only the additive
+ *            answer (impir_answer_add32) uses it
+ *   bytes 4..7 zero
  *   then C_0[2][m+1][16] and C_1[2][m+1][16]: [row = child bit x][column = depth d].
  *   Column 0 holds only the root seed C_0[0][0]; C_0[1][0], C_1[0][0] and C_1[1][0]
  *   must be zero. Total impir_key_bytes(m) = 8 + 64 (m + 1) bytes.
@@ -238,7 +240,9 @@ impir_status impir_server_destroy(impir_server* server);
  * Eval(key0, j) XOR Eval(key1, j) is the 128-bit integer 1 at j = alpha and 0 elsewhere.
  * Randomness: SplitMix64 seeded with the XOR of the four little-endian 64-bit words of
  * rng_seed (draw order: the two roots, then per depth and child bit a uniform codeword
- * and, on the path above the leaves, a uniform offset with lsb 1).
+ * and, on the path above the leaves, a uniform offset with lsb 1). key0 is party 0 and
+ * key1 party 1; the leaf codeword on the path is chosen so that lsb(Eval(key0, alpha)) = 1,
+ * which makes the additive shares (-1)^b low32(Eval(key_b, j)) sum to exactly 1 at alpha.
  * EINVAL: m outside 1..40, alpha >= 2^m, unknown prf, NULL buffers. */
 impir_status dpf_gen(uint64_t alpha, uint32_t m, impir_prf prf, const uint8_t rng_seed[32], uint8_t* key0,
                      uint8_t* key1);

@@ -56,6 +56,9 @@ def _load():
             lib.orc_dpxor.restype = None
             lib.orc_answer.argtypes = [u8p, u8p, ctypes.c_uint64, ctypes.c_uint32, u8p]
             lib.orc_answer_points.argtypes = [u8p, u8p, ctypes.c_uint64, ctypes.c_uint32, u8p]
+            lib.orc_answer_add32.argtypes = [u8p, u8p, ctypes.c_uint64, ctypes.c_uint32, u8p]
+            lib.orc_reconstruct_add32.argtypes = [u8p, u8p, ctypes.c_uint32, u8p]
+            lib.orc_reconstruct_add32.restype = None
             lib.orc_answer_threads.argtypes = [u8p, u8p, ctypes.c_uint64, ctypes.c_uint32, u8p, ctypes.c_int]
             lib.orc_gen.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, u8p, u8p, u8p]
             lib.orc_reconstruct.argtypes = [u8p, u8p, ctypes.c_uint32, u8p]
@@ -169,6 +172,22 @@ def answer_points(key, db: np.ndarray, n_records: int, record_bytes: int) -> byt
     d = np.ascontiguousarray(db, dtype=np.uint8).reshape(-1)
     out = np.zeros(record_bytes, np.uint8)
     _check(_load().orc_answer_points(_ptr(k), _ptr(d), n_records, record_bytes, _ptr(out)), "answer_points")
+    return out.tobytes()
+
+
+def answer_add32(key, db: np.ndarray, n_records: int, record_bytes: int) -> bytes:
+    """Additive answer over Z_{2^32}: sum_j (-1)^party low32(R(m,j)) * D[j], word by word."""
+    k = _u8(key)
+    d = np.ascontiguousarray(db, dtype=np.uint8).reshape(-1)
+    out = np.zeros(record_bytes, np.uint8)
+    _check(_load().orc_answer_add32(_ptr(k), _ptr(d), n_records, record_bytes, _ptr(out)), "answer_add32")
+    return out.tobytes()
+
+
+def reconstruct_add32(r0: bytes, r1: bytes) -> bytes:
+    a, b = _u8(r0), _u8(r1)
+    out = np.zeros(len(a), np.uint8)
+    _load().orc_reconstruct_add32(_ptr(a), _ptr(b), len(a), _ptr(out))
     return out.tobytes()
 
 

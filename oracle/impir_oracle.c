@@ -36,8 +36,9 @@
  *   - Leaves j >= N select nothing; a key with 2^m < N covers the prefix [0, 2^m).
  *
  * Wire format of a key (little-endian), the format both sides parse independently:
- *   byte 0 version = 1, byte 1 prf (0 keyed, 1 MMO), byte 2 m (1..40), byte 3 = 0,
- *   bytes 4..7 = 0, then C_0[2][m+1][16] and then C_1[2][m+1][16], where the first
+ *   byte 0 version = 1, byte 1 prf (0 keyed, 1 MMO), byte 2 m (1..40), byte 3 the party
+ *   index b (0 or 1; only the additive answer uses it), bytes 4..7 = 0, then
+ *   C_0[2][m+1][16] and then C_1[2][m+1][16], where the first
  *   index is the child bit x (row), the second the depth d (column). Column 0 holds
  *   only the root seed C_0[0][0]; C_0[1][0], C_1[0][0], C_1[1][0] must be zero.
  *
@@ -216,6 +217,7 @@ void orc_prf(int prf, const uint8_t s[16], int x, uint8_t out[16]) {
 typedef struct {
     uint32_t m;
     int prf;
+    int party;           /* header byte 3 */
     const uint8_t* C[2]; /* C[t] points at C_t[2][m+1][16] inside the wire key */
 } orc_key;
 
@@ -230,9 +232,10 @@ static int parse_key(const uint8_t* buf, orc_key* k) {
     if (buf[0] != 1) return ORC_EINVAL;
     if (buf[1] > 1) return ORC_EINVAL;
     if (buf[2] < 1 || buf[2] > 40) return ORC_EINVAL;
-    if (buf[3] != 0 || buf[4] != 0 || buf[5] != 0 || buf[6] != 0 || buf[7] != 0) return ORC_EINVAL;
+    if (buf[3] > 1 || buf[4] != 0 || buf[5] != 0 || buf[6] != 0 || buf[7] != 0) return ORC_EINVAL;
     k->m = buf[2];
     k->prf = buf[1];
+    k->party = buf[3];
     k->C[0] = buf + 8;
     k->C[1] = buf + 8 + (size_t)32 * (k->m + 1);
     /* column 0 holds only the root C_0[0][0] */
@@ -380,6 +383,55 @@ int orc_answer_points(const uint8_t* key, const uint8_t* db, uint64_t N, uint32_
     return ORC_OK;
 }
 
+/* The additive (inner-product) answer of §2.2 over Z_{2^32}: records are vectors of
+ * little-endian 32-bit words and server b returns r_b = sum_j v_b[j] * D[j] (mod 2^32, word
+ * by word) with the share v_b[j] = (-1)^b * low32(R(m,j)), low32 being bytes 0..3 of the leaf
+ * read little-endian and b the key's party index. Leaves of the two keys agree off the point
+ * and differ by the integer 1 at it, so the shares sum to 0 off the point and, because Gen
+ * makes lsb(R_0(m, alpha)) = 1, to +1 at it: r_0 + r_1 = D[alpha]. record_bytes must be a
+ * multiple of 4. Every leaf on its own root-to-leaf walk, for any domain size. */
+int orc_answer_add32(const uint8_t* key, const uint8_t* db, uint64_t N, uint32_t record_bytes, uint8_t* out) {
+    orc_key k;
+    int rc = parse_key(key, &k);
+    if (rc) return rc;
+    if (record_bytes == 0 || record_bytes % 4 || N == 0) return ORC_EINVAL;
+    ensure_sbox();
+    uint64_t dom = k.m >= 64 ? UINT64_MAX : ((uint64_t)1 << k.m);
+    uint64_t n = N < dom ? N : dom;
+    uint32_t words = record_bytes / 4;
+    uint32_t* acc = (uint32_t*)calloc(words, sizeof(uint32_t));
+    if (!acc) return ORC_ENOMEM;
+    for (uint64_t j = 0; j < n; j++) {
+        uint8_t leaf[16];
+        node_value(&k, k.m, j, leaf);
+        uint32_t v = (uint32_t)leaf[0] | ((uint32_t)leaf[1] << 8) | ((uint32_t)leaf[2] << 16) | ((uint32_t)leaf[3] << 24);
+        if (k.party) v = 0u - v;
+        const uint8_t* rec = db + j * (uint64_t)record_bytes;
+        for (uint32_t w = 0; w < words; w++) {
+            uint32_t d = (uint32_t)rec[4 * w] | ((uint32_t)rec[4 * w + 1] << 8) | ((uint32_t)rec[4 * w + 2] << 16) |
+                         ((uint32_t)rec[4 * w + 3] << 24);
+            acc[w] += v * d;
+        }
+    }
+    for (uint32_t w = 0; w < words; w++)
+        for (int b = 0; b < 4; b++) out[4 * w + b] = (uint8_t)(acc[w] >> (8 * b));
+    free(acc);
+    return ORC_OK;
+}
+
+/* D[i] = r_0 + r_1 (mod 2^32, word by word): the client side of the additive answer. */
+void orc_reconstruct_add32(const uint8_t* r0, const uint8_t* r1, uint32_t record_bytes, uint8_t* out) {
+    for (uint32_t w = 0; w + 4 <= record_bytes; w += 4) {
+        uint32_t a = 0, b = 0;
+        for (int i = 0; i < 4; i++) {
+            a |= (uint32_t)r0[w + i] << (8 * i);
+            b |= (uint32_t)r1[w + i] << (8 * i);
+        }
+        uint32_t c = a + b;
+        for (int i = 0; i < 4; i++) out[w + i] = (uint8_t)(c >> (8 * i));
+    }
+}
+
 /* ------------------------------------------------------------------------------------
  * Threaded answer: the paper's subtree split (§3.2) + two-stage reduction (§3.3)
  * ---------------------------------------------------------------------------------- */
@@ -525,7 +577,9 @@ static void sm64_block(sm64* g, uint8_t out[16]) {
 /* Gen(alpha) -> (key0, key1) with Eval(key0,j) XOR Eval(key1,j) = [j == alpha] as 128-bit
  * values for every j < 2^m (the DPF property of §2.3 with b = 1).
  * Draw order: s_A, s_B; then for d = 1..m and x = 0, 1: a uniform r, and, when x is the
- * on-path bit and d < m, a uniform delta with lsb forced to 1. */
+ * on-path bit and d < m, a uniform delta with lsb forced to 1. At the leaf on the path the
+ * lsb of r is then set so that lsb(R_A(m, alpha)) = 1, which makes the additive shares of
+ * the two parties (key0 party 0, key1 party 1) sum to +1 rather than -1 at alpha. */
 int orc_gen(uint64_t alpha, uint32_t m, int prf, const uint8_t seed[32], uint8_t* key0, uint8_t* key1) {
     if (m < 1 || m > 40 || (prf != 0 && prf != 1)) return ORC_EINVAL;
     if ((alpha >> m) != 0) return ORC_EINVAL;
@@ -544,6 +598,7 @@ int orc_gen(uint64_t alpha, uint32_t m, int prf, const uint8_t seed[32], uint8_t
         keys[i][0] = 1;
         keys[i][1] = (uint8_t)prf;
         keys[i][2] = (uint8_t)m;
+        keys[i][3] = (uint8_t)i; /* party index */
     }
     /* C_t[x][d] lives at 8 + t*32*(m+1) + (x*(m+1) + d)*16, identical in both keys for d >= 1 */
 #define ORC_CW(key, t, x, d) ((key) + 8 + (size_t)(t) * 32 * (m + 1) + ((size_t)(x) * (m + 1) + (d)) * 16)
@@ -562,6 +617,7 @@ int orc_gen(uint64_t alpha, uint32_t m, int prf, const uint8_t seed[32], uint8_t
             orc_prf(prf, pB, x, fB[x]);
             uint8_t r[16], delta[16] = {0};
             sm64_block(&g, r);
+            if (d == m && x == ad) r[0] = (uint8_t)((r[0] & 0xfe) | ((fA[x][0] & 1) ^ 1)); /* lsb(R_A) = 1 */
             if (x == ad) {
                 if (d < m) {
                     sm64_block(&g, delta);

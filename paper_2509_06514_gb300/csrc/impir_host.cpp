@@ -183,7 +183,8 @@ impir_status parse_host_keys(const uint8_t* keys, uint32_t n, std::vector<uint32
         if (k[0] != IMPIR_KEY_VERSION) return fail(IMPIR_EINVAL, "key %u: version %u", q, k[0]);
         if (k[1] > 1) return fail(IMPIR_EINVAL, "key %u: unknown prf %u", q, k[1]);
         if (m < 1 || m > IMPIR_MAX_DOMAIN_BITS) return fail(IMPIR_EINVAL, "key %u: domain bits %u", q, m);
-        for (int i = 3; i < 8; ++i)
+        if (k[3] > 1) return fail(IMPIR_EINVAL, "key %u: party index %u is not 0 or 1", q, k[3]);
+        for (int i = 4; i < 8; ++i)
             if (k[i]) return fail(IMPIR_EINVAL, "key %u: reserved header byte %d is not zero", q, i);
         const size_t z[3] = {8 + size_t(m + 1) * 16, 8 + size_t(m + 1) * 32, 8 + size_t(m + 1) * 48};
         for (size_t zi : z)
@@ -796,6 +797,8 @@ impir_status dpf_gen(uint64_t alpha, uint32_t m, impir_prf prf, const uint8_t rn
     const size_t kb = impir_key_bytes(m);
     std::memset(key0, 0, kb);
     std::memset(key1, 0, kb);
+    key0[3] = 0;  // party indices
+    key1[3] = 1;
     for (uint8_t* k : {key0, key1}) {
         k[0] = IMPIR_KEY_VERSION;
         k[1] = uint8_t(prf);
@@ -817,6 +820,7 @@ impir_status dpf_gen(uint64_t alpha, uint32_t m, impir_prf prf, const uint8_t rn
             prf_eval(pb, x, fb[x]);
             uint8_t r[16], delta[16] = {0};
             draw(r);
+            if (d == m && x == on) r[0] = uint8_t((r[0] & 0xfe) | ((fa[x][0] & 1) ^ 1));  // lsb(R_A(m, alpha)) = 1
             if (x == on) {
                 if (d < m) {
                     draw(delta);

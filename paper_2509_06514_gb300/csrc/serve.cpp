@@ -295,9 +295,9 @@ impir_status impir_server_create(const impir_server_config* cfg, impir_server** 
 impir_status impir_server_submit(impir_server* S, int32_t db, const uint8_t* key, uint64_t tag) {
     if (!S || !key) return set_error(IMPIR_EINVAL, "NULL argument");
     const uint32_t m = key[2];
-    if (key[0] != IMPIR_KEY_VERSION || key[1] > 1 || m < 1 || m > IMPIR_MAX_DOMAIN_BITS)
+    if (key[0] != IMPIR_KEY_VERSION || key[1] > 1 || m < 1 || m > IMPIR_MAX_DOMAIN_BITS || key[3] > 1)
         return set_error(IMPIR_EINVAL, "malformed key header");
-    for (int i = 3; i < 8; ++i)
+    for (int i = 4; i < 8; ++i)
         if (key[i]) return set_error(IMPIR_EINVAL, "malformed key header");
     uint32_t rb = 0;
     if (impir_db_info(db, nullptr, &rb, nullptr, nullptr) != IMPIR_OK) return set_error(IMPIR_EINVAL, "unknown database");

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(1024) setup_kernel(const SetupParams S) {
             const uint2 h = *reinterpret_cast<const uint2*>(k);
             const uint32_t ver = h.x & 0xffu, prf = (h.x >> 8) & 0xffu;
             m = (h.x >> 16) & 0xffu;
-            ok = ver == 1 && prf <= 1 && m >= 1 && m <= kMaxDomainBits && (h.x >> 24) == 0 && h.y == 0;
+            ok = ver == 1 && prf <= 1 && m >= 1 && m <= kMaxDomainBits && (h.x >> 24) <= 1 && h.y == 0;
             if (ok) {
                 const size_t z[3] = {8 + size_t(m + 1) * 16, 8 + size_t(m + 1) * 32, 8 + size_t(m + 1) * 48};
                 for (int i = 0; i < 3; ++i) {

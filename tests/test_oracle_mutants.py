@@ -44,6 +44,9 @@ MUTANTS = {
     "gen_leaf_offset": ("delta[0] = 1; /* b = 1: the leaves differ by the integer 1 */", "delta[0] = 3;"),
     "gen_path_bit_order": ("int ad = (int)((alpha >> (m - d)) & 1);", "int ad = (int)((alpha >> (d - 1)) & 1);"),
     "threaded_subtree_base": ("uint64_t base = s << h;", "uint64_t base = s << (h - 1);"),
+    "additive_sign_dropped": ("if (k.party) v = 0u - v;", "(void)k.party;"),
+    "additive_share_high_bytes": ("uint32_t v = (uint32_t)leaf[0] | ((uint32_t)leaf[1] << 8)",
+                                  "uint32_t v = (uint32_t)leaf[12] | ((uint32_t)leaf[1] << 8)"),
     "dpxor_range_off_by_one": ("for (uint64_t j = 0; j < n; j++) {\n        if (bits[j] & 1) {",
                                "for (uint64_t j = 1; j < n; j++) {\n        if (bits[j] & 1) {"),
 }
@@ -70,6 +73,9 @@ def build_variant(tmp_path, name, old_new):
     lib.orc_answer.argtypes = [vp, vp, ctypes.c_uint64, ctypes.c_uint32, vp]
     lib.orc_answer_threads.argtypes = [vp, vp, ctypes.c_uint64, ctypes.c_uint32, vp, ctypes.c_int]
     lib.orc_gen.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, vp, vp, vp]
+    lib.orc_answer_add32.argtypes = [vp, vp, ctypes.c_uint64, ctypes.c_uint32, vp]
+    lib.orc_reconstruct_add32.argtypes = [vp, vp, ctypes.c_uint32, vp]
+    lib.orc_reconstruct_add32.restype = None
     return lib
 
 
@@ -164,6 +170,21 @@ def pins(lib):
         lib.orc_dpxor(P(dbs), 9, 5, P(np.ascontiguousarray(sel)), P(o))
         if not np.array_equal(o, want):
             failed.append("dpxor_special")
+            break
+    # additive answer: r_0 + r_1 = D[alpha] (mod 2^32 per word)
+    Na, Ba, ma = 200, 12, 8
+    dba = rng.integers(0, 256, (Na, Ba), dtype=np.uint8)
+    for a in (3, 199):
+        kb = 8 + 64 * (ma + 1)
+        k0, k1 = np.zeros(kb, np.uint8), np.zeros(kb, np.uint8)
+        seed = rng.integers(0, 256, 32, dtype=np.uint8)
+        lib.orc_gen(a, ma, 0, P(seed), P(k0), P(k1))
+        r0, r1, rr = np.zeros(Ba, np.uint8), np.zeros(Ba, np.uint8), np.zeros(Ba, np.uint8)
+        lib.orc_answer_add32(P(k0), P(dba), Na, Ba, P(r0))
+        lib.orc_answer_add32(P(k1), P(dba), Na, Ba, P(r1))
+        lib.orc_reconstruct_add32(P(r0), P(r1), Ba, P(rr))
+        if not np.array_equal(rr, dba[a]):
+            failed.append("additive_reconstruction")
             break
     # reconstruction and the threaded split on a small DB
     N, B, m = 300, 7, 9
