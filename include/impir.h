@@ -110,6 +110,19 @@ impir_status impir_db_version(int32_t db_handle, uint64_t* version);
  * answers come back; the call returns when `out` is written. */
 impir_status impir_answer(int32_t db_handle, const uint8_t* keys, uint32_t n_queries, uint8_t* out);
 
+/* The additive (inner-product) answer of §2.2 over Z_2^32, reconstructed by the client as
+ * r_0 + r_1: records are read as vectors of little-endian 32-bit words (record_bytes must be
+ * a multiple of 4) and the key's party index b (header byte 3) selects the share
+ *   out[q] = sum over j < min(N, 2^m) of (-1)^b * low32(Eval(k, j)) * D[j]   (mod 2^32, per word)
+ * where low32 is bytes 0..3 of the 128-bit leaf read little-endian. Keys from dpf_gen give
+ * r_0 + r_1 = D[alpha]. Same arguments and errors as impir_answer / impir_answer_async, plus
+ * EINVAL when record_bytes is not a multiple of 4. Launch shape: one query per warp tile and
+ * at most 2^5 leaves per lane (one 32-bit share per leaf is kept in shared memory). */
+impir_status impir_answer_add32(int32_t db_handle, const uint8_t* keys, uint32_t n_queries, uint8_t* out);
+impir_status impir_answer_add32_async(int32_t db_handle, const uint8_t* d_keys, const uint32_t* d_key_offsets,
+                                      uint32_t n_queries, uint8_t* d_out, void* d_workspace, size_t workspace_bytes,
+                                      void* cuda_stream);
+
 /* Device workspace an asynchronous answer of n_queries keys against a database of
  * record stride stride_bytes needs (bytes). */
 size_t impir_workspace_bytes(uint32_t n_queries, uint32_t stride_bytes);

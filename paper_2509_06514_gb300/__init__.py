@@ -32,7 +32,7 @@ EXPORTS = [
     "impir_device_sm_count", "impir_timing_enable", "impir_timing_read", "impir_answer_noalloc",
     "impir_server_create", "impir_server_submit", "impir_server_take", "impir_server_stats", "impir_server_destroy",
     "impir_aes_calibrate", "impir_db_update", "impir_db_update_async", "impir_db_version", "impir_server_update",
-    "impir_answer_streamed",
+    "impir_answer_streamed", "impir_answer_add32", "impir_answer_add32_async",
 ]
 
 
@@ -80,6 +80,9 @@ def lib():
                                                  ctypes.POINTER(ctypes.c_void_p)]),
                 "impir_answer": (ctypes.c_int, [ctypes.c_int32, u8p, ctypes.c_uint32, u8p]),
                 "impir_workspace_bytes": (ctypes.c_size_t, [ctypes.c_uint32, ctypes.c_uint32]),
+                "impir_answer_add32": (ctypes.c_int, [ctypes.c_int32, u8p, ctypes.c_uint32, u8p]),
+                "impir_answer_add32_async": (ctypes.c_int, [ctypes.c_int32, vp, vp, ctypes.c_uint32, vp, vp,
+                                                            ctypes.c_size_t, vp]),
                 "impir_answer_async": (ctypes.c_int, [ctypes.c_int32, vp, vp, ctypes.c_uint32, vp, vp,
                                                       ctypes.c_size_t, vp]),
                 "impir_workspace_status": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_uint32),
@@ -209,6 +212,21 @@ def impir_answer_streamed(records, n_records: int, record_bytes: int, keys, n_qu
     _check(lib().impir_answer_streamed(rp, n_records, record_bytes, kp, n_queries, ctypes.c_void_p(out.ctypes.data),
                                        chunk_bytes, ctypes.byref(cfg)), "impir_answer_streamed")
     return out, cfg.as_dict()
+
+
+def impir_answer_add32(db: int, keys, n_queries: int, record_bytes: int) -> np.ndarray:
+    """Additive answer over Z_2^32 (party from each key's header); (n_queries, record_bytes) uint8."""
+    _, kp = _host(keys)
+    out = np.zeros((n_queries, record_bytes), np.uint8)
+    _check(lib().impir_answer_add32(db, kp, n_queries, ctypes.c_void_p(out.ctypes.data)), "impir_answer_add32")
+    return out
+
+
+def impir_answer_add32_async(db: int, d_keys, d_key_offsets, n_queries: int, d_out, d_workspace,
+                             workspace_bytes: int, stream=None) -> None:
+    _check(lib().impir_answer_add32_async(db, _dev(d_keys), _dev(d_key_offsets), n_queries, _dev(d_out),
+                                          _dev(d_workspace), workspace_bytes, _stream(stream)),
+           "impir_answer_add32_async")
 
 
 def impir_workspace_bytes(n_queries: int, stride_bytes: int) -> int:

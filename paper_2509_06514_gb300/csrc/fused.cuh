@@ -180,6 +180,26 @@ __device__ __forceinline__ Blk keyed_one(const Blk p, uint32_t x, uint32_t L) {
     return aes_final(s, L, k.a, k.b, k.c, k.d);
 }
 
+// Word 0 (output bytes 0..3) of both PRF outputs: rounds 1-9 in full, then only column 0
+// of round 10 (the additive answer's shares are the leaves' low 32 bits).
+__device__ __forceinline__ void keyed_leaf_words(const Blk p, uint32_t L, uint32_t& wa, uint32_t& wb) {
+    Key4 k{p.x, p.y, p.z, p.w};
+    Blk a, b;
+    ks_next(k, 0x01u, L);
+    keyed_round1(p, L, k, a, b);
+#pragma unroll 1
+    for (int r = 2; r <= 9; ++r) {
+        ks_next(k, c_rcon[r], L);
+        a = aes_round(a, L, k.a, k.b, k.c, k.d);
+        b = aes_round(b, L, k.a, k.b, k.c, k.d);
+    }
+    const uint32_t k10 = k.a ^ sub_rot(k.d, L) ^ 0x36u;
+    wa = (T<2>(tix(a.x, L, 0)) & 0xffu) ^ (T<3>(tix(a.y, L, 1)) & 0xff00u) ^ (T<0>(tix(a.z, L, 2)) & 0xff0000u) ^
+         (T<1>(tix(a.w, L, 3)) & 0xff000000u) ^ k10;
+    wb = (T<2>(tix(b.x, L, 0)) & 0xffu) ^ (T<3>(tix(b.y, L, 1)) & 0xff00u) ^ (T<0>(tix(b.z, L, 2)) & 0xff0000u) ^
+         (T<1>(tix(b.w, L, 3)) & 0xff000000u) ^ k10;
+}
+
 // ---- MMO PRF: PRF_p(x) = AES_{K_x}(p) ^ p with fixed round keys rk[x][44] ----
 
 __device__ __forceinline__ void mmo_pair(const Blk p, uint32_t L, const uint32_t (&rk)[2][44], const Blk ca,
@@ -209,6 +229,21 @@ __device__ __forceinline__ uint32_t mmo_leaf_bits(const Blk p, uint32_t L, const
     const uint32_t ba = (sbox0_lsb(a9, L) ^ rk[0][40] ^ p.x) & 1u;
     const uint32_t bb = (sbox0_lsb(b9, L) ^ rk[1][40] ^ p.x) & 1u;
     return ba | (bb << 1);
+}
+
+__device__ __forceinline__ void mmo_leaf_words(const Blk p, uint32_t L, const uint32_t (&rk)[2][44], uint32_t& wa,
+                                               uint32_t& wb) {
+    Blk a = {p.x ^ rk[0][0], p.y ^ rk[0][1], p.z ^ rk[0][2], p.w ^ rk[0][3]};
+    Blk b = {p.x ^ rk[1][0], p.y ^ rk[1][1], p.z ^ rk[1][2], p.w ^ rk[1][3]};
+#pragma unroll 1
+    for (int r = 1; r <= 9; ++r) {
+        a = aes_round(a, L, rk[0][4 * r], rk[0][4 * r + 1], rk[0][4 * r + 2], rk[0][4 * r + 3]);
+        b = aes_round(b, L, rk[1][4 * r], rk[1][4 * r + 1], rk[1][4 * r + 2], rk[1][4 * r + 3]);
+    }
+    wa = (T<2>(tix(a.x, L, 0)) & 0xffu) ^ (T<3>(tix(a.y, L, 1)) & 0xff00u) ^ (T<0>(tix(a.z, L, 2)) & 0xff0000u) ^
+         (T<1>(tix(a.w, L, 3)) & 0xff000000u) ^ rk[0][40] ^ p.x;
+    wb = (T<2>(tix(b.x, L, 0)) & 0xffu) ^ (T<3>(tix(b.y, L, 1)) & 0xff00u) ^ (T<0>(tix(b.z, L, 2)) & 0xff0000u) ^
+         (T<1>(tix(b.w, L, 3)) & 0xff000000u) ^ rk[1][40] ^ p.x;
 }
 
 __device__ __forceinline__ Blk mmo_one(const Blk p, uint32_t x, uint32_t L, const uint32_t (&rk)[2][44]) {
@@ -242,7 +277,9 @@ __device__ __forceinline__ uint32_t cw_lsb(const uint8_t* kq, uint32_t m, uint32
 // Selection bits of lane's subtree: root -> depth D walk (Eq. (3) one edge per level), then
 // a depth-first expansion down to the leaves at depth m; bit r of `bits` (relative to the
 // warp tile) is lsb(R(m, tile_first_leaf + r)).
-template <int PRF>
+// MODE 0 writes selection bits; MODE 1 (the additive answer) writes one 32-bit share per
+// leaf, (-1)^party low32(R(m, j)), at word r of `bits`.
+template <int PRF, int MODE>
 __device__ __forceinline__ void lane_eval(const FusedParams& P, const uint8_t* kq, uint32_t m, uint32_t D,
                                           uint64_t sub, uint32_t sq, uint32_t* bits, uint32_t lane, uint32_t L) {
     Blk node = cw_load(kq, m, 0, 0, 0);  // R(0,0) = C_0[0][0], Eq. (2)
@@ -253,8 +290,12 @@ __device__ __forceinline__ void lane_eval(const FusedParams& P, const uint8_t* k
         const Blk f = PRF == 0 ? keyed_one(node, x, L) : mmo_one(node, x, L, P.mmo_rk);
         node = bxor(f, c);
     }
+    const uint32_t neg = kq[3] ? 0xffffffffu : 0u;  // party 1 negates its shares (mod 2^32)
     if (sq == 0) {
-        atomicOr(&bits[lane >> 5], (node.x & 1u) << (lane & 31));
+        if (MODE == 0)
+            atomicOr(&bits[lane >> 5], (node.x & 1u) << (lane & 31));
+        else
+            bits[lane] = (node.x ^ neg) - neg;
         return;
     }
     Blk stk[kMaxLaneBits];
@@ -262,7 +303,22 @@ __device__ __forceinline__ void lane_eval(const FusedParams& P, const uint8_t* k
     const uint32_t npairs = 1u << (sq - 1);
     for (;;) {
         const uint32_t t = node.x & 1u;
-        if (depth == m - 1) {
+        if (depth == m - 1 && MODE == 1) {
+            uint32_t wa, wb;
+            if (PRF == 0)
+                keyed_leaf_words(node, L, wa, wb);
+            else
+                mmo_leaf_words(node, L, P.mmo_rk, wa, wb);
+            wa ^= cw_load(kq, m, t, 0, m).x;
+            wb ^= cw_load(kq, m, t, 1, m).x;
+            const uint32_t r = (lane << sq) + 2 * p;
+            bits[r] = (wa ^ neg) - neg;
+            bits[r + 1] = (wb ^ neg) - neg;
+            ++p;
+            if (p == npairs) break;
+            depth = m - 1 - (__ffs(int(p)) - 1);
+            node = stk[depth - D];
+        } else if (depth == m - 1) {
             uint32_t b2 = PRF == 0 ? keyed_leaf_bits(node, L) : mmo_leaf_bits(node, L, P.mmo_rk);
             b2 ^= cw_lsb(kq, m, t, 0, m) | (cw_lsb(kq, m, t, 1, m) << 1);
             acc |= b2 << ((2 * p) & 31);
@@ -287,7 +343,7 @@ __device__ __forceinline__ void lane_eval(const FusedParams& P, const uint8_t* k
             node = a;
         }
     }
-    if (sq < 5) atomicOr(&bits[(lane << sq) >> 5], acc << ((lane << sq) & 31));
+    if (MODE == 0 && sq < 5) atomicOr(&bits[(lane << sq) >> 5], acc << ((lane << sq) & 31));
 }
 
 __device__ __forceinline__ uint4 ld_db(const uint4* p) { return __ldg(p); }
@@ -415,8 +471,76 @@ __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_ba
     }
 }
 
-template <int QC, int NK>
+__device__ __forceinline__ void mad4(uint4& a, const uint4 v, uint32_t s) {
+    a.x += v.x * s;
+    a.y += v.y * s;
+    a.z += v.z * s;
+    a.w += v.w * s;
+}
+
+__device__ __forceinline__ uint4 add4(const uint4 a, const uint4 b) {
+    return make_uint4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+__device__ __forceinline__ void red_add(uint4* dst, const uint4 v) {
+    uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+    if (v.x) atomicAdd(d, v.x);
+    if (v.y) atomicAdd(d + 1, v.y);
+    if (v.z) atomicAdd(d + 2, v.z);
+    if (v.w) atomicAdd(d + 3, v.w);
+}
+
+// Additive answer of one warp tile for one query: acc += share[r] * D[r] over the tile's
+// records, word by word mod 2^32 (records read as little-endian 32-bit words).
+template <int NK>
+__device__ __forceinline__ void scan_tile_add(const FusedParams& P, uint64_t tile_base, uint32_t nrec,
+                                              const uint32_t* vals, uint32_t qdst, uint4* acc_out, uint32_t lane) {
+    const uint32_t W = P.words;
+    if constexpr (NK == 1) {
+        const uint32_t R = 32u / W, lr = lane / W, lk = lane - lr * W;
+        const bool on = lr < R;
+        uint4 acc = make_uint4(0, 0, 0, 0);
+        const uint4* base = P.db + (tile_base - P.rec_lo) * W + lk;
+#pragma unroll 4
+        for (uint32_t r0 = 0; r0 < nrec; r0 += R) {
+            const uint32_t r = r0 + lr;
+            if (on && r < nrec) mad4(acc, ld_db(base + size_t(r) * W), vals[r]);
+        }
+        if (R * W == 32) {
+            for (uint32_t off = W; off < 32; off <<= 1)
+                acc = add4(acc, make_uint4(__shfl_xor_sync(0xffffffffu, acc.x, off), __shfl_xor_sync(0xffffffffu, acc.y, off),
+                                           __shfl_xor_sync(0xffffffffu, acc.z, off), __shfl_xor_sync(0xffffffffu, acc.w, off)));
+            if (lr == 0) red_add(acc_out + size_t(qdst) * W + lk, acc);
+        } else if (on) {
+            red_add(acc_out + size_t(qdst) * W + lk, acc);
+        }
+    } else {
+        for (uint32_t k0 = 0; k0 < W; k0 += 32 * NK) {
+            uint4 acc[NK];
+#pragma unroll
+            for (int c = 0; c < NK; ++c) acc[c] = make_uint4(0, 0, 0, 0);
+#pragma unroll 2
+            for (uint32_t r = 0; r < nrec; ++r) {
+                const uint32_t sv = vals[r];
+                const uint4* rec = P.db + (tile_base - P.rec_lo + r) * W;
+#pragma unroll
+                for (int c = 0; c < NK; ++c) {
+                    const uint32_t k = k0 + lane + 32 * c;
+                    if (k < W) mad4(acc[c], ld_db(rec + k), sv);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < NK; ++c) {
+                const uint32_t k = k0 + lane + 32 * c;
+                if (k < W) red_add(acc_out + size_t(qdst) * W + k, acc[c]);
+            }
+        }
+    }
+}
+
+template <int QC, int NK, int MODE = 0>
 __global__ void __launch_bounds__(512, 1) fused_kernel(const __grid_constant__ FusedParams P) {
+    static_assert(MODE == 0 || QC == 1, "the additive answer evaluates one query per warp tile");
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
     const uint32_t lane = tid & 31, warp = tid >> 5;
 
@@ -469,8 +593,10 @@ __global__ void __launch_bounds__(512, 1) fused_kernel(const __grid_constant__ F
         const bool lane_on = lane < lanes && (sub << sq) < n_eff;
         const uint32_t nwords = uint32_t((TT + 31) >> 5);
 
-        for (int q = 0; q < QC; ++q)
-            for (uint32_t w = lane; w < nwords; w += 32) bits[q * P.bits_words + w] = 0;
+        if (MODE == 0) {
+            for (int q = 0; q < QC; ++q)
+                for (uint32_t w = lane; w < nwords; w += 32) bits[q * P.bits_words + w] = 0;
+        }
         __syncwarp();
         const uint32_t* qidx = perm + gd.first;
         for (uint32_t qi = 0; qi < gd.count; ++qi) {
@@ -478,24 +604,27 @@ __global__ void __launch_bounds__(512, 1) fused_kernel(const __grid_constant__ F
             const uint32_t prf = kq[1];
             if (lane_on) {
                 if (prf == 0)
-                    lane_eval<0>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L);
+                    lane_eval<0, MODE>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L);
                 else
-                    lane_eval<1>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L);
+                    lane_eval<1, MODE>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L);
             }
         }
         __syncwarp();
-        scan_tile<QC, NK>(P, tile_base, nrec, bits, gd.count, qidx, acc_out, lane);
+        if constexpr (MODE == 0)
+            scan_tile<QC, NK>(P, tile_base, nrec, bits, gd.count, qidx, acc_out, lane);
+        else
+            scan_tile_add<NK>(P, tile_base, nrec, bits, qidx[0], acc_out, lane);
         __syncwarp();
     }
 }
 
 // Sets the dynamic shared memory limit once and launches one instantiation.
-template <int QC, int NK>
+template <int QC, int NK, int MODE = 0>
 cudaError_t launch_fused_t(dim3 grid, dim3 block, size_t smem, cudaStream_t s, const FusedParams& p) {
-    static const cudaError_t attr = cudaFuncSetAttribute(fused_kernel<QC, NK>,
+    static const cudaError_t attr = cudaFuncSetAttribute(fused_kernel<QC, NK, MODE>,
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (attr != cudaSuccess) return attr;
-    fused_kernel<QC, NK><<<grid, block, smem, s>>>(p);
+    fused_kernel<QC, NK, MODE><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -219,8 +219,23 @@ void count_launches(uint64_t n) {
 }
 
 // ---- launches ----
+// Launch shape of the additive answer derived from a configuration: one query per warp tile
+// and a lane subtree small enough for one 32-bit share per leaf in shared memory.
+impir_config add_config(impir_config c) {
+    c.queries_per_warp = 1;
+    while (c.lane_bits > 0 &&
+           kTableBytes + kSegSmemBytes + size_t(c.warps_per_cta) * (size_t(32) << c.lane_bits) * 4 > kSmemMax)
+        --c.lane_bits;
+    return c;
+}
+
+size_t smem_add(const impir_config& c) {
+    return kTableBytes + kSegSmemBytes + size_t(c.warps_per_cta) * (size_t(32) << c.lane_bits) * 4;
+}
+
 impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_config& cfg, const uint8_t* d_keys,
-                          const uint32_t* d_off, uint32_t n, uint8_t* d_out, uint8_t* d_ws, cudaStream_t st) {
+                          const uint32_t* d_off, uint32_t n, uint8_t* d_out, uint8_t* d_ws, cudaStream_t st,
+                          int mode = 0) {
     const WsLayout lay = ws_layout(n, db.stride);
     SetupParams sp{};
     sp.keys = d_keys;
@@ -245,9 +260,9 @@ impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_conf
     fp.n_queries = n;
     fp.words = db.stride / 16;
     fp.lane_bits = cfg.lane_bits;
-    fp.bits_words = 1u << cfg.lane_bits;
+    fp.bits_words = mode == 0 ? 1u << cfg.lane_bits : 32u << cfg.lane_bits;
     std::memcpy(fp.mmo_rk, dev.mmo_rk, sizeof fp.mmo_rk);
-    const size_t smem = smem_for(cfg);
+    const size_t smem = mode == 0 ? smem_for(cfg) : smem_add(cfg);
     const bool timed = timing_on();
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (timed) {
@@ -255,8 +270,12 @@ impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_conf
         CK(cudaEventCreate(&ev1), "event create");
         CK(cudaEventRecord(ev0, st), "event record");
     }
-    CK(launch_fused(cfg.queries_per_warp, nk_for(fp.words), dim3(dev.sms), dim3(cfg.warps_per_cta * 32), smem, st, fp),
-       "fused kernel launch");
+    if (mode == 0)
+        CK(launch_fused(cfg.queries_per_warp, nk_for(fp.words), dim3(dev.sms), dim3(cfg.warps_per_cta * 32), smem, st, fp),
+           "fused kernel launch");
+    else
+        CK(launch_fused_add(nk_for(fp.words), dim3(dev.sms), dim3(cfg.warps_per_cta * 32), smem, st, fp),
+           "fused kernel launch (additive)");
     if (timed) {
         CK(cudaEventRecord(ev1, st), "event record");
         std::lock_guard<std::mutex> lk(g_timing.mu);
@@ -277,26 +296,30 @@ impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_conf
 }
 
 impir_status answer_async_impl(const Db& db, const impir_config* cfg_in, const uint8_t* d_keys, const uint32_t* d_off,
-                               uint32_t n, uint8_t* d_out, void* d_ws, size_t ws_bytes, cudaStream_t st) {
+                               uint32_t n, uint8_t* d_out, void* d_ws, size_t ws_bytes, cudaStream_t st, int mode = 0) {
     DeviceState* dev;
     if (impir_status s = need_device(&dev)) return s;
     if (n == 0) return IMPIR_OK;
     if (!d_keys || !d_off || !d_out || !d_ws) return fail(IMPIR_EINVAL, "NULL device buffer");
     if (reinterpret_cast<uintptr_t>(d_ws) & 255) return fail(IMPIR_EINVAL, "workspace must be 256-byte aligned");
-    const impir_config cfg = cfg_in ? *cfg_in : config_for(db, n, dev->sms);
+    impir_config cfg = cfg_in ? *cfg_in : config_for(db, n, dev->sms);
+    if (mode == 1) {
+        if (db.bytes % 4) return fail(IMPIR_EINVAL, "the additive answer needs records of a multiple of 4 bytes");
+        cfg = add_config(cfg);
+    }
     if (impir_status s = check_config(cfg, db.stride / 16)) return s;
     if (cfg.queries_per_launch == 1) {
         if (ws_bytes < ws_layout(1, db.stride).total) return fail(IMPIR_ENOMEM, "workspace too small");
         for (uint32_t q = 0; q < n; ++q)
             if (impir_status s = launch_batch(*dev, db, cfg, d_keys, d_off + q, 1, d_out + size_t(q) * db.bytes,
-                                              static_cast<uint8_t*>(d_ws), st))
+                                              static_cast<uint8_t*>(d_ws), st, mode))
                 return s;
         return IMPIR_OK;
     }
     if (ws_bytes < ws_layout(n, db.stride).total)
         return fail(IMPIR_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed", ws_bytes,
                     ws_layout(n, db.stride).total);
-    return launch_batch(*dev, db, cfg, d_keys, d_off, n, d_out, static_cast<uint8_t*>(d_ws), st);
+    return launch_batch(*dev, db, cfg, d_keys, d_off, n, d_out, static_cast<uint8_t*>(d_ws), st, mode);
 }
 
 // ---- synchronous path context: cached device and pinned buffers ----
@@ -507,7 +530,7 @@ impir_status impir_workspace_status(const void* d_ws, uint32_t* n_bad, uint32_t*
     return IMPIR_OK;
 }
 
-impir_status impir_answer(int32_t h, const uint8_t* keys, uint32_t n, uint8_t* out) {
+static impir_status answer_sync(int32_t h, const uint8_t* keys, uint32_t n, uint8_t* out, int mode) {
     Db db;
     if (impir_status s = get_db(h, &db)) return s;
     if (n == 0) return IMPIR_OK;
@@ -535,12 +558,27 @@ impir_status impir_answer(int32_t h, const uint8_t* keys, uint32_t n, uint8_t* o
     CK(cudaMemcpyAsync(g_sync.d_off, g_sync.h_stage + total, size_t(n) * 4, cudaMemcpyHostToDevice, st), "offset upload");
     if (impir_status s = answer_async_impl(db, &cfg, static_cast<const uint8_t*>(g_sync.d_keys),
                                            static_cast<const uint32_t*>(g_sync.d_off), n,
-                                           static_cast<uint8_t*>(g_sync.d_out), g_sync.d_ws, g_sync.c_ws, st))
+                                           static_cast<uint8_t*>(g_sync.d_out), g_sync.d_ws, g_sync.c_ws, st, mode))
         return s;
     CK(cudaMemcpyAsync(g_sync.h_stage, g_sync.d_out, out_bytes, cudaMemcpyDeviceToHost, st), "answer download");
     CK(cudaStreamSynchronize(st), "answer");
     std::memcpy(out, g_sync.h_stage, out_bytes);
     return IMPIR_OK;
+}
+
+impir_status impir_answer(int32_t h, const uint8_t* keys, uint32_t n, uint8_t* out) {
+    return answer_sync(h, keys, n, out, 0);
+}
+
+impir_status impir_answer_add32(int32_t h, const uint8_t* keys, uint32_t n, uint8_t* out) {
+    return answer_sync(h, keys, n, out, 1);
+}
+
+impir_status impir_answer_add32_async(int32_t h, const uint8_t* d_keys, const uint32_t* d_off, uint32_t n,
+                                      uint8_t* d_out, void* d_ws, size_t ws_bytes, void* stream) {
+    Db db;
+    if (impir_status s = get_db(h, &db)) return s;
+    return answer_async_impl(db, nullptr, d_keys, d_off, n, d_out, d_ws, ws_bytes, static_cast<cudaStream_t>(stream), 1);
 }
 
 impir_status impir_get_config(int32_t h, uint32_t n_queries, impir_config* cfg) {

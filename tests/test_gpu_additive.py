@@ -1,0 +1,88 @@
+"""GPU parity of the additive (inner-product) answer over Z_2^32 (§2.2's r_1 + r_2): every
+answer equals the oracle's bit for bit, for both parties and PRFs, padded and wide records,
+mixed and tiny domains; the two parties' answers add up to the record."""
+import numpy as np
+import pytest
+
+import paper_2509_06514_gb300 as impir
+from paper_2509_06514_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def built():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2509_06514_gb300 import build
+    build.build()
+
+
+def random_key(rng, m, prf, party):
+    kb = 8 + 64 * (m + 1)
+    k = np.zeros(kb, np.uint8)
+    k[0], k[1], k[2], k[3] = 1, prf, m, party
+    k[8:] = rng.integers(0, 256, kb - 8, dtype=np.uint8)
+    for t, x in ((0, 1), (1, 0), (1, 1)):
+        o = 8 + t * 32 * (m + 1) + (x * (m + 1)) * 16
+        k[o:o + 16] = 0
+    return k.tobytes()
+
+
+@pytest.mark.parametrize("prf", [0, 1])
+@pytest.mark.parametrize("N,B,ms", [
+    (1 << 12, 32, [12, 12, 11, 3]),
+    (3000, 12, [12, 9, 2, 1]),
+    (1 << 11, 1024, [11, 10]),
+    (500, 4100, [9, 8]),
+    (5000, 4, [13, 12]),
+])
+def test_additive_matches_oracle(built, orc, prf, N, B, ms):
+    rng = np.random.default_rng(N + B + 7 * prf)
+    db = workloads.make_db(N, B, seed=N + 3 * B)
+    keys = [random_key(rng, m, prf, i % 2) for i, m in enumerate(ms)]
+    h = impir.impir_db_load(db, N, B)
+    try:
+        got = impir.impir_answer_add32(h, b"".join(keys), len(keys), B)
+        for i, k in enumerate(keys):
+            assert got[i].tobytes() == orc.answer_add32(k, db, N, B), i
+    finally:
+        impir.impir_db_free(h)
+
+
+def test_additive_reconstruction_and_async(built, orc):
+    import torch
+    N, B, m = 20000, 64, 15
+    db = workloads.make_db(N, B, seed=99)
+    rng = np.random.default_rng(99)
+    alphas = [0, 777, 19999]
+    pairs = [impir.dpf_gen(a, m, 0, rng.integers(0, 256, 32, dtype=np.uint8).tobytes()) for a in alphas]
+    h = impir.impir_db_load(db, N, B)
+    try:
+        r0 = impir.impir_answer_add32(h, b"".join(p[0] for p in pairs), 3, B)
+        blob1, offs = impir.pack_keys([p[1] for p in pairs])
+        d_keys = torch.from_numpy(np.frombuffer(blob1, np.uint8).copy()).cuda()
+        d_off = torch.from_numpy(offs.view(np.int32).copy()).cuda()
+        d_out = torch.zeros((3, B), dtype=torch.uint8, device="cuda")
+        wsb = impir.impir_workspace_bytes(3, B)
+        d_ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+        impir.impir_answer_add32_async(h, d_keys, d_off, 3, d_out, d_ws, wsb, None)
+        torch.cuda.synchronize()
+        r1 = d_out.cpu().numpy()
+        for i, a in enumerate(alphas):
+            assert orc.reconstruct_add32(r0[i].tobytes(), r1[i].tobytes()) == db[a].tobytes()
+            assert r1[i].tobytes() == orc.answer_add32(pairs[i][1], db, N, B)
+    finally:
+        impir.impir_db_free(h)
+
+
+def test_additive_rejects_unaligned_records(built):
+    db = workloads.make_db(100, 6, seed=1)
+    h = impir.impir_db_load(db, 100, 6)
+    try:
+        k0, _ = impir.dpf_gen(1, 7, 0, bytes(32))
+        with pytest.raises(impir.ImpirError) as e:
+            impir.impir_answer_add32(h, k0, 1, 6)
+        assert e.value.status == impir.IMPIR_EINVAL
+    finally:
+        impir.impir_db_free(h)
