@@ -193,6 +193,13 @@ impir_status impir_answer_streamed(const void* records, uint64_t n_records, uint
                                    const uint8_t* keys, uint32_t n_queries, uint8_t* out, uint64_t chunk_bytes,
                                    impir_config* used);
 
+/* Saves the process-wide tuning cache to a text file (one entry per line), or merges a saved
+ * one into it (*n_loaded: entries accepted; lines this build cannot launch are skipped), so a
+ * later process's impir_autotune returns without timing anything. EINVAL: unreadable or
+ * unwritable path. */
+impir_status impir_tune_cache_save(const char* path);
+impir_status impir_tune_cache_load(const char* path, uint32_t* n_loaded);
+
 /* ---- Serving: continuous batching over resident databases (§3.4 query batching) ----
  * A server owns `streams` CUDA streams, each with device buffers for one batch of up to
  * max_batch queries. Any thread may submit requests (one key for one registered database,

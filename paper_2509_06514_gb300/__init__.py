@@ -32,7 +32,8 @@ EXPORTS = [
     "impir_device_sm_count", "impir_timing_enable", "impir_timing_read", "impir_answer_noalloc",
     "impir_server_create", "impir_server_submit", "impir_server_take", "impir_server_stats", "impir_server_destroy",
     "impir_aes_calibrate", "impir_db_update", "impir_db_update_async", "impir_db_version", "impir_server_update",
-    "impir_answer_streamed", "impir_answer_add32", "impir_answer_add32_async",
+    "impir_answer_streamed", "impir_answer_add32", "impir_answer_add32_async", "impir_tune_cache_save",
+    "impir_tune_cache_load",
 ]
 
 
@@ -80,6 +81,8 @@ def lib():
                                                  ctypes.POINTER(ctypes.c_void_p)]),
                 "impir_answer": (ctypes.c_int, [ctypes.c_int32, u8p, ctypes.c_uint32, u8p]),
                 "impir_workspace_bytes": (ctypes.c_size_t, [ctypes.c_uint32, ctypes.c_uint32]),
+                "impir_tune_cache_save": (ctypes.c_int, [ctypes.c_char_p]),
+                "impir_tune_cache_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_uint32)]),
                 "impir_answer_add32": (ctypes.c_int, [ctypes.c_int32, u8p, ctypes.c_uint32, u8p]),
                 "impir_answer_add32_async": (ctypes.c_int, [ctypes.c_int32, vp, vp, ctypes.c_uint32, vp, vp,
                                                             ctypes.c_size_t, vp]),
@@ -227,6 +230,16 @@ def impir_answer_add32_async(db: int, d_keys, d_key_offsets, n_queries: int, d_o
     _check(lib().impir_answer_add32_async(db, _dev(d_keys), _dev(d_key_offsets), n_queries, _dev(d_out),
                                           _dev(d_workspace), workspace_bytes, _stream(stream)),
            "impir_answer_add32_async")
+
+
+def impir_tune_cache_save(path: str) -> None:
+    _check(lib().impir_tune_cache_save(path.encode()), "impir_tune_cache_save")
+
+
+def impir_tune_cache_load(path: str) -> int:
+    n = ctypes.c_uint32()
+    _check(lib().impir_tune_cache_load(path.encode(), ctypes.byref(n)), "impir_tune_cache_load")
+    return n.value
 
 
 def impir_workspace_bytes(n_queries: int, stride_bytes: int) -> int:

@@ -786,6 +786,52 @@ impir_status impir_answer_streamed(const void* records, uint64_t N, uint32_t B, 
     return st;
 }
 
+// ---- tuning cache on disk ----
+
+impir_status impir_tune_cache_save(const char* path) {
+    if (!path) return fail(IMPIR_EINVAL, "NULL path");
+    FILE* f = std::fopen(path, "w");
+    if (!f) return fail(IMPIR_EINVAL, "cannot write %s", path);
+    std::fprintf(f, "# impir tuning cache: sms n_records stride_bytes n_queries lane_bits queries_per_warp "
+                    "warps_per_cta queries_per_launch\n");
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (const auto& kv : g_tune)
+            std::fprintf(f, "%d %llu %u %u %u %u %u %u\n", std::get<0>(kv.first),
+                         (unsigned long long)std::get<1>(kv.first), std::get<2>(kv.first), std::get<3>(kv.first),
+                         kv.second.lane_bits, kv.second.queries_per_warp, kv.second.warps_per_cta,
+                         kv.second.queries_per_launch);
+    }
+    std::fclose(f);
+    return IMPIR_OK;
+}
+
+impir_status impir_tune_cache_load(const char* path, uint32_t* n_loaded) {
+    if (!path) return fail(IMPIR_EINVAL, "NULL path");
+    FILE* f = std::fopen(path, "r");
+    if (!f) return fail(IMPIR_EINVAL, "cannot read %s", path);
+    char line[512];
+    uint32_t n = 0;
+    while (std::fgets(line, sizeof line, f)) {
+        if (line[0] == '#') continue;
+        int sms;
+        unsigned long long nrec;
+        unsigned stride, nq;
+        impir_config c{};
+        if (std::sscanf(line, "%d %llu %u %u %u %u %u %u", &sms, &nrec, &stride, &nq, &c.lane_bits,
+                        &c.queries_per_warp, &c.warps_per_cta, &c.queries_per_launch) != 8)
+            continue;
+        if (check_config(c, stride / 16) != IMPIR_OK) continue;  // skip entries this build cannot launch
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[std::make_tuple(sms, uint64_t(nrec), uint32_t(stride), uint32_t(nq))] = c;
+        ++n;
+    }
+    std::fclose(f);
+    g_err.clear();
+    if (n_loaded) *n_loaded = n;
+    return IMPIR_OK;
+}
+
 // ---- client side ----
 
 impir_status impir_reconstruct(const uint8_t* r0, const uint8_t* r1, uint32_t record_bytes, uint8_t* out) {

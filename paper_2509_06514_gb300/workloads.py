@@ -161,6 +161,8 @@ def uneven_8gib(seed: int = 3, n_queries: int = 1024, max_batch: int = 512) -> W
 
 SERVING_DBS = [(1 << 18, 64), (1 << 22, 256), (1 << 24, 512)]
 SERVING_RATES = [5_000, 10_000, 20_000, 50_000, 100_000, 200_000]
+# offered loads below the server's capacity (about 3k queries/s here), for latency context
+SERVING_LOW_RATES = [500, 1_000, 2_000]
 
 
 @dataclass

@@ -92,3 +92,16 @@ def test_workspace_bytes_grows_with_batch(L):
     b = impir.impir_workspace_bytes(1024, 256)
     assert a % 256 == 0 and b % 256 == 0
     assert b - a >= 1023 * 256
+
+
+def test_tune_cache_round_trip(L, tmp_path):
+    src = tmp_path / "tune.txt"
+    src.write_text("# comment\n152 33554432 256 416 8 4 16 0\n152 1048576 256 64 5 8 16 0\n"
+                   "152 1048576 256 65 11 8 16 0\nnot a line\n")
+    assert impir.impir_tune_cache_load(str(src)) == 2          # lane_bits 11 is rejected
+    out = tmp_path / "out.txt"
+    impir.impir_tune_cache_save(str(out))
+    lines = [ln for ln in out.read_text().splitlines() if not ln.startswith("#")]
+    assert "152 33554432 256 416 8 4 16 0" in lines and "152 1048576 256 64 5 8 16 0" in lines
+    with pytest.raises(impir.ImpirError):
+        impir.impir_tune_cache_load(str(tmp_path / "missing.txt"))
