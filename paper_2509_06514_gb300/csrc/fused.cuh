@@ -279,11 +279,14 @@ __device__ __forceinline__ uint32_t cw_lsb(const uint8_t* kq, uint32_t m, uint32
 // warp tile) is lsb(R(m, tile_first_leaf + r)).
 // MODE 0 writes selection bits; MODE 1 (the additive answer) writes one 32-bit share per
 // leaf, (-1)^party low32(R(m, j)), at word r of `bits`.
+// The walk starts from `start`, the node at depth d0 on the lane's path (the root with d0 = 0,
+// or the warp-tile root the warp computed once for this query).
 template <int PRF, int MODE>
 __device__ __forceinline__ void lane_eval(const FusedParams& P, const uint8_t* kq, uint32_t m, uint32_t D,
-                                          uint64_t sub, uint32_t sq, uint32_t* bits, uint32_t lane, uint32_t L) {
-    Blk node = cw_load(kq, m, 0, 0, 0);  // R(0,0) = C_0[0][0], Eq. (2)
-    for (uint32_t d = 1; d <= D; ++d) {
+                                          uint64_t sub, uint32_t sq, uint32_t* bits, uint32_t lane, uint32_t L,
+                                          const Blk start, uint32_t d0) {
+    Blk node = start;
+    for (uint32_t d = d0 + 1; d <= D; ++d) {
         const uint32_t x = uint32_t(sub >> (D - d)) & 1u;
         const uint32_t t = node.x & 1u;
         const Blk c = cw_load(kq, m, t, x, d);
@@ -599,14 +602,30 @@ __global__ void __launch_bounds__(512, 1) fused_kernel(const __grid_constant__ F
         }
         __syncwarp();
         const uint32_t* qidx = perm + gd.first;
+        // Shared top of the walk: the 32 lane subtrees of a warp tile hang below one node at
+        // depth Dt = D - 5; lane q walks root -> that node for query q of the group, so all the
+        // group's queries take one pass, and the nodes are then broadcast to every lane.
+        const uint32_t Dt = D > 5 ? D - 5 : 0;
+        Blk top{0, 0, 0, 0};
+        if (lane < gd.count) {
+            const uint8_t* kq = P.keys + P.key_off[qidx[lane]];
+            top = cw_load(kq, m, 0, 0, 0);  // R(0,0) = C_0[0][0], Eq. (2)
+            for (uint32_t d = 1; d <= Dt; ++d) {
+                const uint32_t x = uint32_t(tile >> (Dt - d)) & 1u;
+                const Blk f = kq[1] == 0 ? keyed_one(top, x, L) : mmo_one(top, x, L, P.mmo_rk);
+                top = bxor(f, cw_load(kq, m, top.x & 1u, x, d));
+            }
+        }
         for (uint32_t qi = 0; qi < gd.count; ++qi) {
             const uint8_t* kq = P.keys + P.key_off[qidx[qi]];
             const uint32_t prf = kq[1];
+            const Blk start{__shfl_sync(0xffffffffu, top.x, qi), __shfl_sync(0xffffffffu, top.y, qi),
+                            __shfl_sync(0xffffffffu, top.z, qi), __shfl_sync(0xffffffffu, top.w, qi)};
             if (lane_on) {
                 if (prf == 0)
-                    lane_eval<0, MODE>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L);
+                    lane_eval<0, MODE>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, Dt);
                 else
-                    lane_eval<1, MODE>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L);
+                    lane_eval<1, MODE>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, Dt);
             }
         }
         __syncwarp();
