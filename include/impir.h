@@ -153,7 +153,8 @@ impir_status impir_workspace_status(const void* d_workspace, uint32_t* n_bad, ui
  *   lane_bits          each lane expands a perfect subtree of 2^lane_bits leaves
  *                      (a warp tile is 32 * 2^lane_bits records); 0..10
  *   queries_per_warp   queries evaluated per warp tile before one shared scan of the
- *                      tile (1, 2, 4 or 8): the DB tile is read once for all of them
+ *                      tile (1, 2, 4, 8, or 16 for records of at most 512 bytes): the DB
+ *                      tile is read once for all of them
  *   warps_per_cta      4..16
  *   queries_per_launch 0 = the whole batch in one persistent launch; 1 = the plain
  *                      one-query-per-launch form (one launch per key, in order) */

@@ -133,8 +133,9 @@ constexpr size_t kSmemMax = 227 * 1024;
 
 impir_status check_config(const impir_config& c, uint32_t words) {
     if (c.lane_bits > kMaxLaneBits) return fail(IMPIR_EINVAL, "lane_bits %u > %u", c.lane_bits, kMaxLaneBits);
-    if (c.queries_per_warp != 1 && c.queries_per_warp != 2 && c.queries_per_warp != 4 && c.queries_per_warp != 8)
-        return fail(IMPIR_EINVAL, "queries_per_warp must be 1, 2, 4 or 8");
+    if (c.queries_per_warp != 1 && c.queries_per_warp != 2 && c.queries_per_warp != 4 && c.queries_per_warp != 8 &&
+        c.queries_per_warp != 16)
+        return fail(IMPIR_EINVAL, "queries_per_warp must be 1, 2, 4, 8 or 16");
     if (c.queries_per_warp * nk_for(words) > 16)
         return fail(IMPIR_EINVAL, "queries_per_warp %u too large for %u-byte records", c.queries_per_warp, words * 16);
     if (c.warps_per_cta < 4 || c.warps_per_cta > 16) return fail(IMPIR_EINVAL, "warps_per_cta must be 4..16");
@@ -619,7 +620,7 @@ impir_status impir_autotune(int32_t h, const uint8_t* d_keys, const uint32_t* d_
     }
     const impir_config base = default_config(db.n, db.stride / 16, n, dev->sms);
     std::vector<impir_config> cands;
-    for (uint32_t qpw : {1u, 2u, 4u, 8u}) {
+    for (uint32_t qpw : {1u, 2u, 4u, 8u, 16u}) {
         if (qpw > 1 && qpw / 2 >= n) continue;
         for (int ds = -3; ds <= 2; ++ds) {
             const int s = int(base.lane_bits) + ds;

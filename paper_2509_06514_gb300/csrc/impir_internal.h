@@ -114,13 +114,14 @@ struct FinalizeParams {
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_setup(const SetupParams& p, cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t s);
-// qpw in {1,2,4,8}, nk in {1,2,4,8} with qpw * nk <= 16.
+// qpw in {1,2,4,8,16}, nk in {1,2,4,8} with qpw * nk <= 16.
 cudaError_t launch_fused(uint32_t qpw, uint32_t nk, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                          const FusedParams& p);
 cudaError_t launch_fused_q1(uint32_t nk, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const FusedParams& p);
 cudaError_t launch_fused_q2(uint32_t nk, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const FusedParams& p);
 cudaError_t launch_fused_q4(uint32_t nk, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const FusedParams& p);
 cudaError_t launch_fused_add(uint32_t nk, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const FusedParams& p);
+cudaError_t launch_fused_q16(uint32_t nk, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const FusedParams& p);
 cudaError_t launch_fused_q8(uint32_t nk, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const FusedParams& p);
 
 // Host AES pieces of the product (independent of the oracle): T-table and key schedule.

@@ -162,6 +162,7 @@ cudaError_t launch_fused(uint32_t qpw, uint32_t nk, dim3 grid, dim3 block, size_
         case 2: return launch_fused_q2(nk, grid, block, smem, s, p);
         case 4: return launch_fused_q4(nk, grid, block, smem, s, p);
         case 8: return launch_fused_q8(nk, grid, block, smem, s, p);
+        case 16: return launch_fused_q16(nk, grid, block, smem, s, p);
         default: return cudaErrorInvalidValue;
     }
 }
