@@ -91,7 +91,10 @@ extern "C" impir_status impir_aes_calibrate(int prf, uint32_t iters, uint32_t n_
         *ms = f;
         if (e == cudaSuccess) e = cudaMemcpy(out, d_out, nb, cudaMemcpyDeviceToHost);
     }
-    if (e != cudaSuccess) st = set_error(IMPIR_ECUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        st = set_error(IMPIR_ECUDA, cudaGetErrorString(e));
+    }
     cudaFree(d_te0);
     cudaFree(d_seeds);
     cudaFree(d_out);

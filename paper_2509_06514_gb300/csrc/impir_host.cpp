@@ -41,7 +41,10 @@ impir_status fail(impir_status st, const char* fmt, ...) {
     return st;
 }
 
+// A failed runtime call also sets the runtime's last error; consume it so that the next
+// unrelated CUDA call in the process (ours or the caller's) does not report it again.
 impir_status cuda_fail(cudaError_t e, const char* what) {
+    cudaGetLastError();
     return fail(IMPIR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
@@ -347,7 +350,10 @@ impir_status grow(void** p, size_t* cap, size_t need, bool pinned = false) {
         *cap = 0;
     }
     cudaError_t e = pinned ? cudaMallocHost(p, n) : cudaMalloc(p, n);
-    if (e != cudaSuccess) return fail(IMPIR_ENOMEM, "allocation of %zu bytes failed: %s", n, cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(IMPIR_ENOMEM, "allocation of %zu bytes failed: %s", n, cudaGetErrorString(e));
+    }
     *cap = n;
     return IMPIR_OK;
 }
@@ -409,8 +415,11 @@ impir_status impir_db_load(const void* records, uint64_t n_records, uint32_t rec
     const uint32_t stride = (record_bytes + 15u) & ~15u;
     void* d = nullptr;
     cudaError_t e = cudaMalloc(&d, size_t(n_records) * stride);
-    if (e != cudaSuccess) return fail(IMPIR_ENOMEM, "device allocation of %llu bytes failed: %s",
-                                      (unsigned long long)(n_records * stride), cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(IMPIR_ENOMEM, "device allocation of %llu bytes failed: %s",
+                    (unsigned long long)(n_records * stride), cudaGetErrorString(e));
+    }
     if (stride != record_bytes) {
         e = cudaMemset(d, 0, size_t(n_records) * stride);
         if (e == cudaSuccess)
@@ -719,6 +728,7 @@ impir_status impir_answer_streamed(const void* records, uint64_t N, uint32_t B, 
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, offs.data(), size_t(n) * 4, cudaMemcpyHostToDevice, ks);
     if (e != cudaSuccess) {
         cleanup();
+        cudaGetLastError();
         return fail(e == cudaErrorMemoryAllocation ? IMPIR_ENOMEM : IMPIR_ECUDA, "streamed answer setup: %s",
                     cudaGetErrorString(e));
     }

@@ -132,7 +132,10 @@ extern "C" impir_status impir_answer_noalloc(const void* d_records, uint64_t n_r
     sp.words = words;
     sp.lane_bits = lane_bits;
     sp.qpw = qpw;
-    if (launch_setup(sp, st) != cudaSuccess) return set_error(IMPIR_ECUDA, "setup kernel launch failed");
+    if (launch_setup(sp, st) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(IMPIR_ECUDA, "setup kernel launch failed");
+    }
 
     FusedParams fp{};
     fp.db = static_cast<const uint4*>(d_records);
@@ -148,8 +151,10 @@ extern "C" impir_status impir_answer_noalloc(const void* d_records, uint64_t n_r
     fp.bits_words = 1u << lane_bits;
     for (int x = 0; x < 2; ++x)
         for (int i = 0; i < 44; ++i) fp.mmo_rk[x][i] = dev->mmo_rk[x][i];
-    if (launch_fused(qpw, nk, dim3(dev->sms), dim3(warps * 32), smem, st, fp) != cudaSuccess)
+    if (launch_fused(qpw, nk, dim3(dev->sms), dim3(warps * 32), smem, st, fp) != cudaSuccess) {
+        cudaGetLastError();
         return set_error(IMPIR_ECUDA, "fused kernel launch failed");
+    }
 
     FinalizeParams zp{};
     zp.ws = dev->scratch;
@@ -158,6 +163,9 @@ extern "C" impir_status impir_answer_noalloc(const void* d_records, uint64_t n_r
     zp.n_queries = n_queries;
     zp.record_bytes = record_bytes;
     zp.stride = stride_bytes;
-    if (launch_finalize(zp, st) != cudaSuccess) return set_error(IMPIR_ECUDA, "finalize kernel launch failed");
+    if (launch_finalize(zp, st) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(IMPIR_ECUDA, "finalize kernel launch failed");
+    }
     return IMPIR_OK;
 }

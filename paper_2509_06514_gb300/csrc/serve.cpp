@@ -277,6 +277,7 @@ impir_status impir_server_create(const impir_server_config* cfg, impir_server** 
         if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&s.h_in), kb + size_t(cfg->max_batch) * 4);
         if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&s.h_out), size_t(cfg->max_batch) * stride);
         if (e != cudaSuccess) {
+            cudaGetLastError();
             for (Slot& t : S->slots) free_slot(t);
             delete S;
             return set_error(IMPIR_ENOMEM, "server buffers could not be allocated");
