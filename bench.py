@@ -428,19 +428,22 @@ def main():
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
             run_step()
-        g.replay()
-        stream.synchronize()
-        same = all(np.array_equal(bt["d_out"].cpu().numpy(), a) for bt, a in zip(batches, ans0))
-        gs, ge = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        gs.record(stream)
-        for _ in range(args.steps):
+        with torch.cuda.stream(stream):          # replay() launches on the current stream
             g.replay()
-        ge.record(stream)
-        ge.synchronize()
+            stream.synchronize()
+            same = all(np.array_equal(bt["d_out"].cpu().numpy(), a) for bt, a in zip(batches, ans0))
+            gs, ge = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            gs.record(stream)
+            for _ in range(args.steps):
+                g.replay()
+            ge.record(stream)
+            ge.synchronize()
+        torch.cuda.synchronize()
         graph = {"value": nq * args.steps / (gs.elapsed_time(ge) / 1e3), "unit": "queries/s",
                  "bit_identical": same}
         del g
     except Exception as e:  # capture needs the library's launches only; report why if it fails
+        torch.cuda.synchronize()
         graph = {"error": str(e)[:200]}
 
     # ---- e2e: the synchronous C-ABI call with host buffers (H2D keys, D2H answers inside) ----

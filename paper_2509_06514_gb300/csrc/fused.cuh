@@ -596,7 +596,13 @@ __global__ void __launch_bounds__(512, 1) fused_kernel(const __grid_constant__ F
         const bool lane_on = lane < lanes && (sub << sq) < n_eff;
         const uint32_t nwords = uint32_t((TT + 31) >> 5);
 
-        if (MODE == 0) {
+        // Cooperative walk (selection-bit answers, lane subtrees of >= 64 leaves, at most 8
+        // queries per warp: with 16 the kernel sits at its register limit and runs slower): the warp
+        // expands the 5 levels between the warp-tile root and the lane subtree roots for all
+        // the group's queries at once, level by level, in place in the (not yet used) bit area;
+        // otherwise each lane walks them itself for every query.
+        const bool coop = MODE == 0 && QC <= 8 && P.bits_words >= 64 && m >= 5;
+        if (MODE == 0 && !coop) {
             for (int q = 0; q < QC; ++q)
                 for (uint32_t w = lane; w < nwords; w += 32) bits[q * P.bits_words + w] = 0;
         }
@@ -616,16 +622,66 @@ __global__ void __launch_bounds__(512, 1) fused_kernel(const __grid_constant__ F
                 top = bxor(f, cw_load(kq, m, top.x & 1u, x, d));
             }
         }
-        for (uint32_t qi = 0; qi < gd.count; ++qi) {
-            const uint8_t* kq = P.keys + P.key_off[qidx[qi]];
-            const uint32_t prf = kq[1];
-            const Blk start{__shfl_sync(0xffffffffu, top.x, qi), __shfl_sync(0xffffffffu, top.y, qi),
-                            __shfl_sync(0xffffffffu, top.z, qi), __shfl_sync(0xffffffffu, top.w, qi)};
-            if (lane_on) {
-                if (prf == 0)
-                    lane_eval<0, MODE>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, Dt);
-                else
-                    lane_eval<1, MODE>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, Dt);
+        if (coop) {
+            uint8_t* nodes = reinterpret_cast<uint8_t*>(bits);  // query q's nodes at q * slot
+            const uint32_t slot = P.bits_words * 4;
+            if (lane < gd.count) *reinterpret_cast<uint4*>(nodes + lane * slot) = make_uint4(top.x, top.y, top.z, top.w);
+            __syncwarp();
+            for (uint32_t k = 0; k < 4; ++k) {  // level k -> k + 1 below the warp-tile root
+                const uint32_t per = 1u << k, items = gd.count * per;
+                // parents in descending index order: children 2i, 2i+1 overwrite only parents
+                // already read (in this chunk, before any write) or expanded (earlier chunks)
+                for (uint32_t f0 = 0; f0 < items; f0 += 32) {
+                    const uint32_t f = f0 + lane;
+                    const bool act = f < items;
+                    const uint32_t q = act ? f % gd.count : 0, i = act ? (per - 1) - f / gd.count : 0;
+                    uint4 pv = make_uint4(0, 0, 0, 0);
+                    if (act) pv = *reinterpret_cast<const uint4*>(nodes + q * slot + i * 16);
+                    __syncwarp();
+                    if (act) {
+                        const uint8_t* kq = P.keys + P.key_off[qidx[q]];
+                        const Blk par{pv.x, pv.y, pv.z, pv.w};
+                        const uint32_t t = par.x & 1u, d = Dt + k + 1;
+                        const Blk c0 = cw_load(kq, m, t, 0, d), c1 = cw_load(kq, m, t, 1, d);
+                        Blk a, b;
+                        if (kq[1] == 0)
+                            keyed_pair(par, L, c0, c1, a, b);
+                        else
+                            mmo_pair(par, L, P.mmo_rk, c0, c1, a, b);
+                        *reinterpret_cast<uint4*>(nodes + q * slot + (2 * i) * 16) = make_uint4(a.x, a.y, a.z, a.w);
+                        *reinterpret_cast<uint4*>(nodes + q * slot + (2 * i + 1) * 16) = make_uint4(b.x, b.y, b.z, b.w);
+                    }
+                    __syncwarp();
+                }
+            }
+            for (uint32_t qi = 0; qi < gd.count; ++qi) {
+                const uint8_t* kq = P.keys + P.key_off[qidx[qi]];
+                const uint32_t prf = kq[1];
+                // lane l's parent at level 4 is node l >> 1; its subtree root is child l & 1
+                const uint4 pv = *reinterpret_cast<const uint4*>(nodes + qi * slot + (lane >> 1) * 16);
+                __syncwarp();
+                for (uint32_t w = lane; w < nwords; w += 32) bits[qi * P.bits_words + w] = 0;
+                __syncwarp();
+                const Blk start{pv.x, pv.y, pv.z, pv.w};
+                if (lane_on) {
+                    if (prf == 0)
+                        lane_eval<0, MODE>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, D - 1);
+                    else
+                        lane_eval<1, MODE>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, D - 1);
+                }
+            }
+        } else {
+            for (uint32_t qi = 0; qi < gd.count; ++qi) {
+                const uint8_t* kq = P.keys + P.key_off[qidx[qi]];
+                const uint32_t prf = kq[1];
+                const Blk start{__shfl_sync(0xffffffffu, top.x, qi), __shfl_sync(0xffffffffu, top.y, qi),
+                                __shfl_sync(0xffffffffu, top.z, qi), __shfl_sync(0xffffffffu, top.w, qi)};
+                if (lane_on) {
+                    if (prf == 0)
+                        lane_eval<0, MODE>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, Dt);
+                    else
+                        lane_eval<1, MODE>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, Dt);
+                }
             }
         }
         __syncwarp();
