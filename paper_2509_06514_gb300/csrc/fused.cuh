@@ -388,6 +388,10 @@ __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_ba
         // W <= 32: R records per step, lane -> (record lr, word lk)
         const uint32_t R = 32u / W, lr = lane / W, lk = lane - lr * W;
         const bool on = lr < R;
+        // 1 << R, from a value the compiler cannot see through, so that multiplying by it stays an
+        // integer multiply-add (FMA pipe) instead of becoming a shift (ALU pipe, which the AES
+        // engine keeps busy)
+        const uint32_t stepmul = (P.n_queries != 0 ? 1u : 0u) << R;
         uint4 acc[QC];
 #pragma unroll
         for (int q = 0; q < QC; ++q) acc[q] = make_uint4(0, 0, 0, 0);
@@ -407,14 +411,19 @@ __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_ba
                         if ((sel[q] >> i) & 1u) acc[q] = bxor4(acc[q], v);
                 }
             } else {
+                // bit-reversed selection words: step i's bit sits in bit 31 of sh << i, so a step
+                // takes one arithmetic shift for the mask and one multiply by 2^R to advance
+                uint32_t sh[QC];
+#pragma unroll
+                for (int q = 0; q < QC; ++q) sh[q] = __brev(sel[q]);
 #pragma unroll 4
                 for (uint32_t i = 0; i < 32; i += R) {
                     const uint32_t r = c0 + i + lr;
                     const uint4 v = (on && i + lr < nloc) ? ld_db(base + size_t(r) * W) : make_uint4(0, 0, 0, 0);
 #pragma unroll
                     for (int q = 0; q < QC; ++q) {
-                        const uint32_t msk = uint32_t(int32_t(sel[q] << (31u - i)) >> 31);
-                        xor_masked(acc[q], v, msk);
+                        xor_masked(acc[q], v, uint32_t(int32_t(sh[q]) >> 31));
+                        asm("mul.lo.u32 %0, %0, %1;" : "+r"(sh[q]) : "r"(stepmul));
                     }
                 }
             }
