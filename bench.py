@@ -584,6 +584,7 @@ def main():
         serving = run_serving(args, impir, workloads)
 
     if rank == 0:
+        traffic = captured_traffic(cfg, w.name)
         out = {
             "metric": "PIR queries/s (DPF eval+dpXOR) at 8 GiB DB", "value": value, "unit": "queries/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -597,12 +598,14 @@ def main():
             "clocks": clocks,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GAES/s",
                          "frac": (achieved / peak) if achieved else None,
-                         "traffic": captured_traffic(cfg, w.name),
+                         "traffic": traffic,
                          "peak_basis": f"{sms} SMs x {mhz:.0f} MHz x {SMEM_LOOKUPS_PER_CLK_PER_SM} table lookups/clk"
                                        f" / {LOOKUPS_PER_BLOCK_KEYED} lookups per keyed AES block",
                          "kernel": "fused_kernel", "avg_launch_ms": launch_ms, "launches": fused_launches},
-            "scan": {"logical_gbs": scan_bytes * args.steps / (ms / 1e3) / 1e9, "hbm_peak_gbs": pk.get("hbm_gbs"),
-                     "peak_kind": pk_kind},
+            "scan": {"logical_gbs": scan_bytes * args.steps / (ms / 1e3) / 1e9,
+                     # DRAM bytes of one fused launch (ncu capture) over its live duration
+                     "physical_gbs": (traffic / (launch_ms / 1e3) / 1e9) if traffic and launch_ms else None,
+                     "hbm_peak_gbs": pk.get("hbm_gbs"), "peak_kind": pk_kind},
             "aes_blocks_per_s": blocks_per_step * args.steps / (ms / 1e3),
             "aes_engine": engine,
             "one_query_per_launch": plain,
