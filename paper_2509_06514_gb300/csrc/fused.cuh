@@ -274,17 +274,119 @@ __device__ __forceinline__ uint32_t cw_lsb(const uint8_t* kq, uint32_t m, uint32
     return __ldg(kq + cw_off(m, t, x, d)) & 1u;
 }
 
+__device__ __forceinline__ uint4 ld_db(const uint4* p) { return __ldg(p); }
+
+__device__ __forceinline__ void mad4(uint4& a, const uint4 v, uint32_t s) {
+    a.x += v.x * s;
+    a.y += v.y * s;
+    a.z += v.z * s;
+    a.w += v.w * s;
+}
+
+__device__ __forceinline__ uint4 add4(const uint4 a, const uint4 b) {
+    return make_uint4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+__device__ __forceinline__ void red_add(uint4* dst, const uint4 v) {
+    uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+    if (v.x) atomicAdd(d, v.x);
+    if (v.y) atomicAdd(d + 1, v.y);
+    if (v.z) atomicAdd(d + 2, v.z);
+    if (v.w) atomicAdd(d + 3, v.w);
+}
+
+// Additive answer of one chunk of a warp tile for one query: acc += share * D[r], word by word
+// mod 2^32 (records read as little-endian 32-bit words), added into the query's accumulator.
+// The chunk holds `runs` runs of `run_len` consecutive records; run l starts at tile record
+// (l << sq) + chunk_off and its shares sit at vals[l * run_len ...]. Records at or past `nrec`
+// (the DB end) are skipped; runs start in ascending order.
+template <int NK>
+__device__ __forceinline__ void scan_chunk_add(const FusedParams& P, uint64_t tile_base, uint32_t nrec,
+                                               const uint32_t* vals, uint32_t runs, uint32_t run_len, uint32_t sq,
+                                               uint32_t chunk_off, uint32_t qdst, uint4* acc_out, uint32_t lane) {
+    const uint32_t W = P.words;
+    const uint4* tile = P.db + (tile_base - P.rec_lo) * W;
+    if constexpr (NK == 1) {
+        // W <= 32: R records per step, lane -> (record lr, word lk)
+        const uint32_t R = 32u / W, lr = lane / W, lk = lane - lr * W;
+        const bool on = lr < R;
+        uint4 acc = make_uint4(0, 0, 0, 0);
+        for (uint32_t l = 0; l < runs; ++l) {
+            const uint32_t rb = (l << sq) + chunk_off;
+            if (rb >= nrec) break;
+            const uint32_t n = min(run_len, nrec - rb);
+            const uint32_t* vl = vals + l * run_len;
+            const uint4* bl = tile + size_t(rb) * W + lk;
+            // eight records' loads in flight per lane before their multiply-adds: the scan
+            // streams the tile from L2 and has little arithmetic per load to hide latency behind
+            for (uint32_t r0 = 0; r0 < n; r0 += 8 * R) {
+                uint4 v[8];
+                uint32_t sv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const uint32_t r = r0 + u * R + lr;
+                    const bool ok = on && r < n;
+                    v[u] = ok ? ld_db(bl + size_t(r) * W) : make_uint4(0, 0, 0, 0);
+                    sv[u] = ok ? vl[r] : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) mad4(acc, v[u], sv[u]);
+            }
+        }
+        if (R * W == 32) {
+            for (uint32_t off = W; off < 32; off <<= 1)
+                acc = add4(acc, make_uint4(__shfl_xor_sync(0xffffffffu, acc.x, off), __shfl_xor_sync(0xffffffffu, acc.y, off),
+                                           __shfl_xor_sync(0xffffffffu, acc.z, off), __shfl_xor_sync(0xffffffffu, acc.w, off)));
+            if (lr == 0) red_add(acc_out + size_t(qdst) * W + lk, acc);
+        } else if (on) {
+            red_add(acc_out + size_t(qdst) * W + lk, acc);
+        }
+    } else {
+        // W > 32: the whole warp reads one record per step, NK words per lane, in column passes
+        for (uint32_t k0 = 0; k0 < W; k0 += 32 * NK) {
+            uint4 acc[NK];
+#pragma unroll
+            for (int c = 0; c < NK; ++c) acc[c] = make_uint4(0, 0, 0, 0);
+            for (uint32_t l = 0; l < runs; ++l) {
+                const uint32_t rb = (l << sq) + chunk_off;
+                if (rb >= nrec) break;
+                const uint32_t n = min(run_len, nrec - rb);
+                const uint32_t* vl = vals + l * run_len;
+#pragma unroll 4
+                for (uint32_t r = 0; r < n; ++r) {
+                    const uint32_t sv = vl[r];
+                    const uint4* rec = tile + size_t(rb + r) * W;
+#pragma unroll
+                    for (int c = 0; c < NK; ++c) {
+                        const uint32_t k = k0 + lane + 32 * c;
+                        if (k < W) mad4(acc[c], ld_db(rec + k), sv);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < NK; ++c) {
+                const uint32_t k = k0 + lane + 32 * c;
+                if (k < W) red_add(acc_out + size_t(qdst) * W + k, acc[c]);
+            }
+        }
+    }
+}
+
 // Selection bits of lane's subtree: root -> depth D walk (Eq. (3) one edge per level), then
 // a depth-first expansion down to the leaves at depth m; bit r of `bits` (relative to the
 // warp tile) is lsb(R(m, tile_first_leaf + r)).
-// MODE 0 writes selection bits; MODE 1 (the additive answer) writes one 32-bit share per
-// leaf, (-1)^party low32(R(m, j)), at word r of `bits`.
+// MODE 0 writes selection bits. MODE 1 (the additive answer) computes one 32-bit share per
+// leaf, (-1)^party low32(R(m, j)), into a buffer of 32 leaves per lane (one chunk), and the
+// warp scans the chunk's records whenever the buffer is full: lane subtrees can be larger than
+// the buffer, and in MODE 1 every lane of the warp must call this function (lanes past the DB
+// end walk nodes that exist in the tree; the scan skips their records).
 // The walk starts from `start`, the node at depth d0 on the lane's path (the root with d0 = 0,
 // or the warp-tile root the warp computed once for this query).
-template <int PRF, int MODE>
+template <int PRF, int MODE, int NK = 1>
 __device__ __forceinline__ void lane_eval(const FusedParams& P, const uint8_t* kq, uint32_t m, uint32_t D,
                                           uint64_t sub, uint32_t sq, uint32_t* bits, uint32_t lane, uint32_t L,
-                                          const Blk start, uint32_t d0) {
+                                          const Blk start, uint32_t d0, uint64_t tile_base = 0, uint32_t nrec = 0,
+                                          uint32_t qdst = 0, uint4* acc_out = nullptr) {
     Blk node = start;
     for (uint32_t d = d0 + 1; d <= D; ++d) {
         const uint32_t x = uint32_t(sub >> (D - d)) & 1u;
@@ -295,12 +397,19 @@ __device__ __forceinline__ void lane_eval(const FusedParams& P, const uint8_t* k
     }
     const uint32_t neg = kq[3] ? 0xffffffffu : 0u;  // party 1 negates its shares (mod 2^32)
     if (sq == 0) {
-        if (MODE == 0)
+        if (MODE == 0) {
             atomicOr(&bits[lane >> 5], (node.x & 1u) << (lane & 31));
-        else
+        } else {
             bits[lane] = (node.x ^ neg) - neg;
+            __syncwarp();
+            scan_chunk_add<NK>(P, tile_base, nrec, bits, 1, 32, 0, 0, qdst, acc_out, lane);
+        }
         return;
     }
+    // MODE 1 chunks: ch leaves per lane; with lane subtrees of at most 32 leaves the chunk is
+    // the whole tile (one run of consecutive records), else 32 runs of 32 records
+    const uint32_t ch_bits = sq < 5 ? sq : 5u, ch = 1u << ch_bits;
+    const uint32_t runs = sq > 5 ? 32u : 1u, run_len = sq > 5 ? 32u : (32u << sq);
     Blk stk[kMaxLaneBits];
     uint32_t depth = D, p = 0, acc = 0;
     const uint32_t npairs = 1u << (sq - 1);
@@ -314,9 +423,14 @@ __device__ __forceinline__ void lane_eval(const FusedParams& P, const uint8_t* k
                 mmo_leaf_words(node, L, P.mmo_rk, wa, wb);
             wa ^= cw_load(kq, m, t, 0, m).x;
             wb ^= cw_load(kq, m, t, 1, m).x;
-            const uint32_t r = (lane << sq) + 2 * p;
+            const uint32_t o = (2 * p) & (ch - 1), r = (lane << ch_bits) + o;
             bits[r] = (wa ^ neg) - neg;
             bits[r + 1] = (wb ^ neg) - neg;
+            if (o + 2 == ch) {  // chunk full: scan its records (all lanes arrive here together)
+                __syncwarp();
+                scan_chunk_add<NK>(P, tile_base, nrec, bits, runs, run_len, sq, 2 * p + 2 - ch, qdst, acc_out, lane);
+                __syncwarp();
+            }
             ++p;
             if (p == npairs) break;
             depth = m - 1 - (__ffs(int(p)) - 1);
@@ -348,8 +462,6 @@ __device__ __forceinline__ void lane_eval(const FusedParams& P, const uint8_t* k
     }
     if (MODE == 0 && sq < 5) atomicOr(&bits[(lane << sq) >> 5], acc << ((lane << sq) & 31));
 }
-
-__device__ __forceinline__ uint4 ld_db(const uint4* p) { return __ldg(p); }
 
 __device__ __forceinline__ void red_xor(uint4* dst, const uint4 v) {
     if (v.x | v.y)
@@ -483,72 +595,7 @@ __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_ba
     }
 }
 
-__device__ __forceinline__ void mad4(uint4& a, const uint4 v, uint32_t s) {
-    a.x += v.x * s;
-    a.y += v.y * s;
-    a.z += v.z * s;
-    a.w += v.w * s;
-}
 
-__device__ __forceinline__ uint4 add4(const uint4 a, const uint4 b) {
-    return make_uint4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
-}
-
-__device__ __forceinline__ void red_add(uint4* dst, const uint4 v) {
-    uint32_t* d = reinterpret_cast<uint32_t*>(dst);
-    if (v.x) atomicAdd(d, v.x);
-    if (v.y) atomicAdd(d + 1, v.y);
-    if (v.z) atomicAdd(d + 2, v.z);
-    if (v.w) atomicAdd(d + 3, v.w);
-}
-
-// Additive answer of one warp tile for one query: acc += share[r] * D[r] over the tile's
-// records, word by word mod 2^32 (records read as little-endian 32-bit words).
-template <int NK>
-__device__ __forceinline__ void scan_tile_add(const FusedParams& P, uint64_t tile_base, uint32_t nrec,
-                                              const uint32_t* vals, uint32_t qdst, uint4* acc_out, uint32_t lane) {
-    const uint32_t W = P.words;
-    if constexpr (NK == 1) {
-        const uint32_t R = 32u / W, lr = lane / W, lk = lane - lr * W;
-        const bool on = lr < R;
-        uint4 acc = make_uint4(0, 0, 0, 0);
-        const uint4* base = P.db + (tile_base - P.rec_lo) * W + lk;
-#pragma unroll 4
-        for (uint32_t r0 = 0; r0 < nrec; r0 += R) {
-            const uint32_t r = r0 + lr;
-            if (on && r < nrec) mad4(acc, ld_db(base + size_t(r) * W), vals[r]);
-        }
-        if (R * W == 32) {
-            for (uint32_t off = W; off < 32; off <<= 1)
-                acc = add4(acc, make_uint4(__shfl_xor_sync(0xffffffffu, acc.x, off), __shfl_xor_sync(0xffffffffu, acc.y, off),
-                                           __shfl_xor_sync(0xffffffffu, acc.z, off), __shfl_xor_sync(0xffffffffu, acc.w, off)));
-            if (lr == 0) red_add(acc_out + size_t(qdst) * W + lk, acc);
-        } else if (on) {
-            red_add(acc_out + size_t(qdst) * W + lk, acc);
-        }
-    } else {
-        for (uint32_t k0 = 0; k0 < W; k0 += 32 * NK) {
-            uint4 acc[NK];
-#pragma unroll
-            for (int c = 0; c < NK; ++c) acc[c] = make_uint4(0, 0, 0, 0);
-#pragma unroll 2
-            for (uint32_t r = 0; r < nrec; ++r) {
-                const uint32_t sv = vals[r];
-                const uint4* rec = P.db + (tile_base - P.rec_lo + r) * W;
-#pragma unroll
-                for (int c = 0; c < NK; ++c) {
-                    const uint32_t k = k0 + lane + 32 * c;
-                    if (k < W) mad4(acc[c], ld_db(rec + k), sv);
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < NK; ++c) {
-                const uint32_t k = k0 + lane + 32 * c;
-                if (k < W) red_add(acc_out + size_t(qdst) * W + k, acc[c]);
-            }
-        }
-    }
-}
 
 template <int QC, int NK, int MODE = 0>
 __global__ void __launch_bounds__(512, 1) fused_kernel(const __grid_constant__ FusedParams P) {
@@ -685,19 +732,18 @@ __global__ void __launch_bounds__(512, 1) fused_kernel(const __grid_constant__ F
                 const uint32_t prf = kq[1];
                 const Blk start{__shfl_sync(0xffffffffu, top.x, qi), __shfl_sync(0xffffffffu, top.y, qi),
                                 __shfl_sync(0xffffffffu, top.z, qi), __shfl_sync(0xffffffffu, top.w, qi)};
-                if (lane_on) {
+                if (MODE == 1 || lane_on) {  // MODE 1 scans inside the walk: the whole warp takes part
                     if (prf == 0)
-                        lane_eval<0, MODE>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, Dt);
+                        lane_eval<0, MODE, NK>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, Dt,
+                                               tile_base, nrec, qidx[qi], acc_out);
                     else
-                        lane_eval<1, MODE>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, Dt);
+                        lane_eval<1, MODE, NK>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, Dt,
+                                               tile_base, nrec, qidx[qi], acc_out);
                 }
             }
         }
         __syncwarp();
-        if constexpr (MODE == 0)
-            scan_tile<QC, NK>(P, tile_base, nrec, bits, gd.count, qidx, acc_out, lane);
-        else
-            scan_tile_add<NK>(P, tile_base, nrec, bits, qidx[0], acc_out, lane);
+        if constexpr (MODE == 0) scan_tile<QC, NK>(P, tile_base, nrec, bits, gd.count, qidx, acc_out, lane);
         __syncwarp();
     }
 }

@@ -225,16 +225,17 @@ void count_launches(uint64_t n) {
 // ---- launches ----
 // Launch shape of the additive answer derived from a configuration: one query per warp tile
 // and a lane subtree small enough for one 32-bit share per leaf in shared memory.
+// The additive answer keeps one 32-bit share per leaf for at most 32 leaves per lane at a time
+// (larger lane subtrees are scanned in chunks), one query per warp tile.
+uint32_t add_share_words(const impir_config& c) { return 32u << (c.lane_bits < 5 ? c.lane_bits : 5u); }
+
 impir_config add_config(impir_config c) {
     c.queries_per_warp = 1;
-    while (c.lane_bits > 0 &&
-           kTableBytes + kSegSmemBytes + size_t(c.warps_per_cta) * (size_t(32) << c.lane_bits) * 4 > kSmemMax)
-        --c.lane_bits;
     return c;
 }
 
 size_t smem_add(const impir_config& c) {
-    return kTableBytes + kSegSmemBytes + size_t(c.warps_per_cta) * (size_t(32) << c.lane_bits) * 4;
+    return kTableBytes + kSegSmemBytes + size_t(c.warps_per_cta) * add_share_words(c) * 4;
 }
 
 impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_config& cfg, const uint8_t* d_keys,
@@ -264,7 +265,7 @@ impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_conf
     fp.n_queries = n;
     fp.words = db.stride / 16;
     fp.lane_bits = cfg.lane_bits;
-    fp.bits_words = mode == 0 ? 1u << cfg.lane_bits : 32u << cfg.lane_bits;
+    fp.bits_words = mode == 0 ? 1u << cfg.lane_bits : add_share_words(cfg);
     std::memcpy(fp.mmo_rk, dev.mmo_rk, sizeof fp.mmo_rk);
     const size_t smem = mode == 0 ? smem_for(cfg) : smem_add(cfg);
     const bool timed = timing_on();

@@ -50,6 +50,25 @@ def test_additive_matches_oracle(built, orc, prf, N, B, ms):
         impir.impir_db_free(h)
 
 
+@pytest.mark.parametrize("lane_bits", [5, 6, 7, 8, 10])
+@pytest.mark.parametrize("N,B", [(40000, 256), (33000, 12), (21000, 1024), (9000, 4100)])
+def test_additive_chunked_lane_subtrees(built, orc, lane_bits, N, B):
+    """Lane subtrees of 32..1024 leaves (scanned in chunks of 32 leaves per lane) over a ragged
+    DB end, narrow, wide and multi-pass records, both PRFs and parties, domains larger than N."""
+    rng = np.random.default_rng(lane_bits * 131 + N + B)
+    db = workloads.make_db(N, B, seed=N ^ B)
+    ms = [16, 16, 15, 17]
+    keys = [random_key(rng, m, i % 2, (i >> 1) % 2) for i, m in enumerate(ms)]
+    h = impir.impir_db_load(db, N, B)
+    try:
+        impir.impir_set_config(h, lane_bits, 1, 16, 0)
+        got = impir.impir_answer_add32(h, b"".join(keys), len(keys), B)
+        for i, k in enumerate(keys):
+            assert got[i].tobytes() == orc.answer_add32(k, db, N, B), (i, ms[i])
+    finally:
+        impir.impir_db_free(h)
+
+
 def test_additive_reconstruction_and_async(built, orc):
     import torch
     N, B, m = 20000, 64, 15
