@@ -528,15 +528,22 @@ __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_ba
                 uint32_t sh[QC];
 #pragma unroll
                 for (int q = 0; q < QC; ++q) sh[q] = __brev(sel[q]);
-#pragma unroll 4
-                for (uint32_t i = 0; i < 32; i += R) {
-                    const uint32_t r = c0 + i + lr;
-                    const uint4 v = (on && i + lr < nloc) ? ld_db(base + size_t(r) * W) : make_uint4(0, 0, 0, 0);
+                // four steps' loads in flight before their XORs
+                for (uint32_t i0 = 0; i0 < 32; i0 += 4 * R) {
+                    uint4 v[4];
 #pragma unroll
-                    for (int q = 0; q < QC; ++q) {
-                        xor_masked(acc[q], v, uint32_t(int32_t(sh[q]) >> 31));
-                        asm("mul.lo.u32 %0, %0, %1;" : "+r"(sh[q]) : "r"(stepmul));
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t i = i0 + u * R;
+                        v[u] = (on && i < 32 && i + lr < nloc) ? ld_db(base + size_t(c0 + i + lr) * W)
+                                                               : make_uint4(0, 0, 0, 0);
                     }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int q = 0; q < QC; ++q) {
+                            xor_masked(acc[q], v[u], uint32_t(int32_t(sh[q]) >> 31));
+                            asm("mul.lo.u32 %0, %0, %1;" : "+r"(sh[q]) : "r"(stepmul));
+                        }
                 }
             }
         }

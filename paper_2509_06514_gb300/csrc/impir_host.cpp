@@ -234,6 +234,25 @@ impir_config add_config(impir_config c) {
     return c;
 }
 
+// Default shape of the additive answer (one query per unit): the largest lane subtree, up to
+// 256 leaves, that still leaves three units per resident warp.
+impir_config default_add_config(uint64_t n_records, uint32_t n_queries, int sms) {
+    impir_config c{};
+    c.warps_per_cta = 16;
+    c.queries_per_warp = 1;
+    c.queries_per_launch = 0;
+    const double warps = double(sms) * c.warps_per_cta;
+    c.lane_bits = 0;
+    for (uint32_t s = 8; s > 0; --s) {
+        const double tiles = std::ceil(double(n_records) / double(32ull << s));
+        if (double(n_queries) * tiles >= 3.0 * warps) {
+            c.lane_bits = s;
+            break;
+        }
+    }
+    return c;
+}
+
 size_t smem_add(const impir_config& c) {
     return kTableBytes + kSegSmemBytes + size_t(c.warps_per_cta) * add_share_words(c) * 4;
 }
@@ -307,7 +326,9 @@ impir_status answer_async_impl(const Db& db, const impir_config* cfg_in, const u
     if (n == 0) return IMPIR_OK;
     if (!d_keys || !d_off || !d_out || !d_ws) return fail(IMPIR_EINVAL, "NULL device buffer");
     if (reinterpret_cast<uintptr_t>(d_ws) & 255) return fail(IMPIR_EINVAL, "workspace must be 256-byte aligned");
-    impir_config cfg = cfg_in ? *cfg_in : config_for(db, n, dev->sms);
+    impir_config cfg = cfg_in                      ? *cfg_in
+                       : (mode == 1 && !db.cfg_set) ? default_add_config(db.n, n, dev->sms)
+                                                    : config_for(db, n, dev->sms);
     if (mode == 1) {
         if (db.bytes % 4) return fail(IMPIR_EINVAL, "the additive answer needs records of a multiple of 4 bytes");
         cfg = add_config(cfg);
