@@ -184,12 +184,17 @@ impir_status impir_autotune(int32_t db_handle, const uint8_t* d_keys, const uint
 /* Database larger than device memory (§3.3: evaluate the linear operations over the DB in
  * batches of chunks): answers n_queries host keys against n_records records of record_bytes
  * each that stay in host memory `records`, streaming them through the device in chunks of
- * about chunk_bytes (rounded to whole warp tiles), two chunk buffers deep, the copy of one
- * chunk overlapping the fused launch on the previous one; per-query accumulators persist
- * across chunks. Same answers as impir_answer on the same records. Pinned host memory
- * (cudaHostAlloc / cudaHostRegister) lets the copies run at full link bandwidth. `out` is
- * host memory of n_queries * record_bytes bytes; *used (may be NULL) receives the launch
- * shape. Allocates its buffers for the call and frees them before returning. */
+ * about chunk_bytes (rounded to whole warp tiles; the first chunk a quarter of that), two
+ * chunk buffers deep, the copy of one chunk overlapping the fused launches on earlier ones.
+ * Consecutive chunks alternate between two compute streams with their own work schedules, so
+ * one chunk's launch starts on the SMs the previous one frees; per-query accumulators are
+ * shared and persist across chunks. Same answers as impir_answer on the same records. Pinned
+ * host memory (cudaHostAlloc / cudaHostRegister) lets the copies run at full link bandwidth.
+ * `out` is host memory of n_queries * record_bytes bytes; *used (may be NULL) receives the
+ * launch shape. The two chunk buffers (2 x chunk_bytes of device memory), the workspace, the
+ * streams and the events are allocated by the first call that needs them and kept for later
+ * calls (grown when a call needs more); calls are serialised on an internal lock. ENOMEM when
+ * the buffers cannot be allocated. */
 impir_status impir_answer_streamed(const void* records, uint64_t n_records, uint32_t record_bytes,
                                    const uint8_t* keys, uint32_t n_queries, uint8_t* out, uint64_t chunk_bytes,
                                    impir_config* used);

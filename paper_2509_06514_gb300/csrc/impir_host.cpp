@@ -360,6 +360,33 @@ struct SyncCtx {
 
 SyncCtx g_sync;
 
+// ---- streamed path context: staging buffers, workspace, streams and events kept for reuse ----
+struct StreamCtx {
+    std::mutex mu;
+    void *d_buf[2] = {nullptr, nullptr}, *d_keys = nullptr, *d_off = nullptr, *d_ws = nullptr, *d_out = nullptr;
+    size_t c_buf[2] = {0, 0}, c_keys = 0, c_off = 0, c_ws = 0, c_out = 0;
+    uint32_t zeroed_stride = 0;  // padding of both buffers is zero for this record layout (0: unknown)
+    cudaStream_t cs = nullptr, ks[2] = {nullptr, nullptr};
+    cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr}, ready = nullptr, done1 = nullptr;
+    bool ok = false;
+};
+
+StreamCtx g_streamed;
+
+cudaError_t streamed_ctx_init(StreamCtx& c) {
+    if (c.ok) return cudaSuccess;
+    cudaError_t e = cudaStreamCreateWithFlags(&c.cs, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&c.ks[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.copied[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.consumed[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.done1, cudaEventDisableTiming);
+    c.ok = e == cudaSuccess;
+    return e;
+}
+
 impir_status grow(void** p, size_t* cap, size_t need, bool pinned = false) {
     if (*cap >= need) return IMPIR_OK;
     size_t n = std::max(need, *cap * 2);
@@ -710,68 +737,79 @@ impir_status impir_answer_streamed(const void* records, uint64_t N, uint32_t B, 
     uint64_t chunk = (chunk_bytes / stride) / T * T;
     if (chunk < T) chunk = T;
     if (chunk > N) chunk = (N + T - 1) / T * T;
-    const uint64_t nchunks = (N + chunk - 1) / chunk;
+    // chunk boundaries: a quarter-size first chunk (the only copy nothing overlaps), then full ones
+    std::vector<uint64_t> bounds{0};
+    const uint64_t first = std::max(T, chunk / 4 / T * T);
+    for (uint64_t lo = 0; lo < N;) {
+        lo = std::min(N, lo + (bounds.size() == 1 ? first : chunk));
+        bounds.push_back(lo);
+    }
+    const uint64_t nchunks = bounds.size() - 1;
+    // Two work schedules, one per compute stream, so that a chunk's launch can start on the SMs
+    // the previous chunk's launch frees in its tail; both accumulate into the same answers. One
+    // allocation [schedule 1 | schedule 0 | accumulators]: schedule 0 is the usual layout at
+    // offset D = lay.off_acc, schedule 1 sits at offset 0 with its accumulator offset moved by D.
     const WsLayout lay = ws_layout(n, stride);
+    WsLayout lay1 = lay;
+    lay1.off_acc = 2 * lay.off_acc;
+    lay1.total = lay.total + lay.off_acc;
 
-    uint8_t *d_keys = nullptr, *d_ws = nullptr, *d_out = nullptr, *d_buf[2] = {nullptr, nullptr};
-    uint32_t* d_off = nullptr;
-    cudaStream_t cs = nullptr, ks = nullptr;
-    cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+    StreamCtx& X = g_streamed;
+    std::lock_guard<std::mutex> lk(X.mu);
+    if (cudaError_t e = streamed_ctx_init(X)) return cuda_fail(e, "streamed answer streams");
+    const size_t buf_bytes = chunk * stride;
+    const bool regrow = X.c_buf[0] < buf_bytes || X.c_buf[1] < buf_bytes;
+    for (int i = 0; i < 2; ++i)
+        if (impir_status s = grow(&X.d_buf[i], &X.c_buf[i], buf_bytes)) return s;
+    if (impir_status s = grow(&X.d_keys, &X.c_keys, total)) return s;
+    if (impir_status s = grow(&X.d_off, &X.c_off, size_t(n) * 4)) return s;
+    if (impir_status s = grow(&X.d_ws, &X.c_ws, lay1.total)) return s;
+    if (impir_status s = grow(&X.d_out, &X.c_out, size_t(n) * B)) return s;
+    uint8_t* d_buf[2] = {static_cast<uint8_t*>(X.d_buf[0]), static_cast<uint8_t*>(X.d_buf[1])};
+    uint8_t* d_keys = static_cast<uint8_t*>(X.d_keys);
+    uint32_t* d_off = static_cast<uint32_t*>(X.d_off);
+    uint8_t* d_ws = static_cast<uint8_t*>(X.d_ws);
+    uint8_t* d_out = static_cast<uint8_t*>(X.d_out);
+    cudaStream_t cs = X.cs, *ks = X.ks;
+    cudaEvent_t *copied = X.copied, *consumed = X.consumed, ready = X.ready, done1 = X.done1;
     impir_status st = IMPIR_OK;
-    auto cleanup = [&]() {
-        if (cs) cudaStreamSynchronize(cs);
-        if (ks) cudaStreamSynchronize(ks);
-        cudaFree(d_keys);
-        cudaFree(d_off);
-        cudaFree(d_ws);
-        cudaFree(d_out);
-        cudaFree(d_buf[0]);
-        cudaFree(d_buf[1]);
-        for (int i = 0; i < 2; ++i) {
-            if (copied[i]) cudaEventDestroy(copied[i]);
-            if (consumed[i]) cudaEventDestroy(consumed[i]);
-        }
-        if (cs) cudaStreamDestroy(cs);
-        if (ks) cudaStreamDestroy(ks);
-    };
-    cudaError_t e = cudaMalloc(&d_keys, total);
-    if (e == cudaSuccess) e = cudaMalloc(&d_off, size_t(n) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&d_ws, lay.total);
-    if (e == cudaSuccess) e = cudaMalloc(&d_out, size_t(n) * B);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-        e = cudaMalloc(&d_buf[i], chunk * stride);
-        if (e == cudaSuccess) e = cudaMemset(d_buf[i], 0, chunk * stride);  // padding bytes stay zero
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&consumed[i], cudaEventDisableTiming);
+    cudaError_t e = cudaSuccess;
+    // records with padding: the copies write B of every `stride` bytes, the rest must read as zero
+    // (a call without padding writes whole rows and leaves the buffers' contents arbitrary)
+    if (stride == B) {
+        X.zeroed_stride = 0;
+    } else if (regrow || X.zeroed_stride != stride) {
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMemsetAsync(d_buf[i], 0, X.c_buf[i], cs);
+        if (e == cudaSuccess) X.zeroed_stride = stride;
     }
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ks, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_keys, keys, total, cudaMemcpyHostToDevice, ks);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, offs.data(), size_t(n) * 4, cudaMemcpyHostToDevice, ks);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_keys, keys, total, cudaMemcpyHostToDevice, ks[0]);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, offs.data(), size_t(n) * 4, cudaMemcpyHostToDevice, ks[0]);
     if (e != cudaSuccess) {
-        cleanup();
-        cudaGetLastError();
-        return fail(e == cudaErrorMemoryAllocation ? IMPIR_ENOMEM : IMPIR_ECUDA, "streamed answer setup: %s",
-                    cudaGetErrorString(e));
+        X.zeroed_stride = 0;
+        return cuda_fail(e, "streamed answer setup");
     }
+    uint8_t* const ws_of[2] = {d_ws + lay.off_acc, d_ws};
+    const WsLayout* const lay_of[2] = {&lay, &lay1};
     const uint8_t* src = static_cast<const uint8_t*>(records);
     for (uint64_t c = 0; c < nchunks && e == cudaSuccess; ++c) {
-        const int b = int(c & 1);
-        const uint64_t lo = c * chunk, cnt = std::min(chunk, N - lo);
+        const int b = int(c & 1);  // buffer, compute stream and schedule of this chunk
+        const uint64_t lo = bounds[c], cnt = bounds[c + 1] - lo;
         // copy stream: refill buffer b once the launch two chunks back has read it
         if (c >= 2) e = cudaStreamWaitEvent(cs, consumed[b], 0);
         if (e == cudaSuccess)
             e = stride == B ? cudaMemcpyAsync(d_buf[b], src + lo * B, cnt * B, cudaMemcpyHostToDevice, cs)
                             : cudaMemcpy2DAsync(d_buf[b], stride, src + lo * B, B, B, cnt, cudaMemcpyHostToDevice, cs);
         if (e == cudaSuccess) e = cudaEventRecord(copied[b], cs);
-        // compute stream: this chunk's warp tiles, accumulating into the same answers
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(ks, copied[b], 0);
+        // compute stream b: this chunk's warp tiles, accumulating into the shared answers
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ks[b], copied[b], 0);
+        // stream 1 starts after stream 0 has the keys and has zeroed the accumulators
+        if (e == cudaSuccess && c == 1) e = cudaStreamWaitEvent(ks[1], ready, 0);
         if (e != cudaSuccess) break;
         SetupParams sp{};
         sp.keys = d_keys;
         sp.key_off = d_off;
-        sp.ws = d_ws;
-        sp.lay = lay;
+        sp.ws = ws_of[b];
+        sp.lay = *lay_of[b];
         sp.n_records = N;
         sp.n_queries = n;
         sp.words = words;
@@ -780,14 +818,15 @@ impir_status impir_answer_streamed(const void* records, uint64_t N, uint32_t B, 
         sp.tile_lo = lo / T;
         sp.tile_hi = (lo + cnt + T - 1) / T;
         sp.keep_acc = c > 0;
-        e = launch_setup(sp, ks);
+        e = launch_setup(sp, ks[b]);
+        if (e == cudaSuccess && c == 0) e = cudaEventRecord(ready, ks[0]);
         FusedParams fp{};
         fp.db = reinterpret_cast<const uint4*>(d_buf[b]);
         fp.keys = d_keys;
         fp.key_off = d_off;
-        fp.ws = d_ws;
+        fp.ws = ws_of[b];
         fp.te0 = dev->d_te0;
-        fp.lay = lay;
+        fp.lay = *lay_of[b];
         fp.n_records = N;
         fp.n_queries = n;
         fp.words = words;
@@ -797,25 +836,34 @@ impir_status impir_answer_streamed(const void* records, uint64_t N, uint32_t B, 
         std::memcpy(fp.mmo_rk, dev->mmo_rk, sizeof fp.mmo_rk);
         if (e == cudaSuccess)
             e = launch_fused(cfg.queries_per_warp, nk_for(words), dim3(dev->sms), dim3(cfg.warps_per_cta * 32),
-                             smem_for(cfg), ks, fp);
-        if (e == cudaSuccess) e = cudaEventRecord(consumed[b], ks);
+                             smem_for(cfg), ks[b], fp);
+        if (e == cudaSuccess) e = cudaEventRecord(consumed[b], ks[b]);
         count_launches(2);
     }
+    // join: stream 0 finalizes once stream 1's launches are done
+    if (e == cudaSuccess) e = cudaEventRecord(done1, ks[1]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ks[0], done1, 0);
     if (e == cudaSuccess) {
         FinalizeParams zp{};
-        zp.ws = d_ws;
+        zp.ws = ws_of[0];
         zp.lay = lay;
         zp.out = d_out;
         zp.n_queries = n;
         zp.record_bytes = B;
         zp.stride = stride;
-        e = launch_finalize(zp, ks);
+        e = launch_finalize(zp, ks[0]);
         count_launches(1);
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, size_t(n) * B, cudaMemcpyDeviceToHost, ks);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ks);
-    if (e != cudaSuccess) st = cuda_fail(e, "streamed answer");
-    cleanup();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, size_t(n) * B, cudaMemcpyDeviceToHost, ks[0]);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ks[0]);
+    if (e != cudaSuccess) {
+        // leave no work of this call behind on the cached streams
+        cudaStreamSynchronize(cs);
+        cudaStreamSynchronize(ks[0]);
+        cudaStreamSynchronize(ks[1]);
+        X.zeroed_stride = 0;
+        st = cuda_fail(e, "streamed answer");
+    }
     return st;
 }
 

@@ -27,6 +27,7 @@ def keys_for(rng, N, ms, prf=0):
     (1 << 20, 256, 16 << 20, [20] * 24 + [19, 18, 12, 3]),
     (300001, 40, 5 << 20, [19, 19, 17, 12, 19]),
     (70000, 1024, 1, [17, 16, 10]),          # chunk rounded up to one warp tile
+    (5000, 64, 1 << 30, [13, 12, 5]),        # chunk larger than the DB
 ])
 def test_streamed_equals_resident(built, orc, N, B, chunk_bytes, ms):
     rng = np.random.default_rng(N + B)
@@ -57,3 +58,20 @@ def test_streamed_from_pinned_memory_reconstructs(built):
     r1, _ = impir.impir_answer_streamed(pinned.data_ptr(), N, B, b"".join(p[1] for p in pairs), 3, 4 << 20)
     for i, a in enumerate(alphas):
         assert np.array_equal(r0[i] ^ r1[i], db[a])
+
+
+def test_streamed_buffer_reuse_across_layouts(built):
+    """The staging buffers are kept between calls: a padded layout (40 B records, 48 B rows),
+    then whole 48 B rows that overwrite the padding, then the padded layout again; every call
+    equals the resident answers."""
+    rng = np.random.default_rng(77)
+    for N, B in ((90000, 40), (90000, 48), (90000, 40), (1 << 16, 256), (90000, 40)):
+        db = workloads.make_db(N, B, seed=N + B + 1)
+        pairs = keys_for(rng, N, [17, 16, 14])
+        blob = b"".join(p[0] for p in pairs)
+        got, _ = impir.impir_answer_streamed(db, N, B, blob, len(pairs), 1 << 20)
+        h = impir.impir_db_load(db, N, B)
+        try:
+            assert np.array_equal(got, impir.impir_answer(h, blob, len(pairs), B)), (N, B)
+        finally:
+            impir.impir_db_free(h)
