@@ -40,6 +40,7 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=WORKLOADS, default="uneven8g")
+    p.add_argument("--queries", type=int, default=None, help="query count of the batched256m workload (default 64)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true", help="skip the one-query-per-launch comparison")
     p.add_argument("--no-tune", action="store_true")
@@ -52,8 +53,10 @@ def parse_args():
     return p.parse_args()
 
 
-def make_workload(name):
+def make_workload(name, queries=None):
     from paper_2509_06514_gb300 import workloads as W
+    if name == "batched256m" and queries:
+        return W.batched_256mib(n_queries=queries)
     return {"uneven8g": W.uneven_8gib, "batched4g": W.batched_4gib, "batched256m": W.batched_256mib,
             "single": W.single_query}[name]()
 
@@ -199,7 +202,7 @@ def run_reference(args, world, rank):
     import oracle
     from paper_2509_06514_gb300 import workloads
     oracle.build()
-    w = make_workload(args.workload)
+    w = make_workload(args.workload, args.queries)
     cores = os.cpu_count() or 1
     # one query per step, taken round-robin from the workload (records regenerated once)
     db = workloads.make_db(w.n_records, w.record_bytes, w.db_seed)
@@ -338,7 +341,7 @@ def main():
 
     torch.cuda.set_device(local)
     build.build()
-    w = make_workload(args.workload)
+    w = make_workload(args.workload, args.queries)
     N, B = w.n_records, w.record_bytes
     t_setup = time.perf_counter()
     db = workloads.make_db(N, B, w.db_seed)
@@ -576,7 +579,9 @@ def main():
         acfg = impir.impir_get_config(dbh, len(sub)).as_dict()
         additive = {"queries": len(sub), "add32_queries_per_s": len(sub) / t_add, "xor_queries_per_s": len(sub) / t_xor,
                     "reconstructed_ok": ok,
-                    "launch": {"lane_bits": acfg["lane_bits"], "queries_per_warp": 1, "warps_per_cta": acfg["warps_per_cta"]}}
+                    # the library narrows the additive launch to one query per warp and <= 16 warps
+                    "launch": {"lane_bits": acfg["lane_bits"], "queries_per_warp": 1,
+                               "warps_per_cta": min(acfg["warps_per_cta"], 16)}}
 
     # bulk update bandwidth: 256 MiB of new records into the resident DB (synchronous call)
     upd_n = min((256 << 20) // B, N // 2)

@@ -155,7 +155,8 @@ impir_status impir_workspace_status(const void* d_workspace, uint32_t* n_bad, ui
  *   queries_per_warp   queries evaluated per warp tile before one shared scan of the
  *                      tile (1, 2, 4, 8, or 16 for records of at most 512 bytes): the DB
  *                      tile is read once for all of them
- *   warps_per_cta      4..16
+ *   warps_per_cta      4..16; up to 20 for the XOR answer with records of at most 512 bytes
+ *                      and at most 8 queries per warp (the additive answer uses at most 16)
  *   queries_per_launch 0 = the whole batch in one persistent launch; 1 = the plain
  *                      one-query-per-launch form (one launch per key, in order) */
 typedef struct {

@@ -605,7 +605,10 @@ __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_ba
 
 
 template <int QC, int NK, int MODE = 0>
-__global__ void __launch_bounds__(512, 1) fused_kernel(const __grid_constant__ FusedParams P) {
+// Up to 640 threads (20 warps) for the XOR answer with one column pass and at most 8 queries
+// per warp, which fit in 102 registers; 512 for the others, which need more.
+__global__ void __launch_bounds__((MODE == 0 && NK == 1 && QC <= 8) ? 640 : 512, 1)
+    fused_kernel(const __grid_constant__ FusedParams P) {
     static_assert(MODE == 0 || QC == 1, "the additive answer evaluates one query per warp tile");
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
     const uint32_t lane = tid & 31, warp = tid >> 5;

@@ -128,6 +128,10 @@ uint32_t nk_for(uint32_t words) {
     return need <= 2 ? 2 : need <= 4 ? 4 : 8;
 }
 
+// Widest CTA the fused kernel is built for (its launch bounds): 20 warps for the XOR answer
+// with one column pass (records of at most 512 bytes) and at most 8 queries per warp, else 16.
+uint32_t max_warps(uint32_t qpw, uint32_t words) { return nk_for(words) == 1 && qpw <= 8 ? 20u : 16u; }
+
 size_t smem_for(const impir_config& c) {
     return kTableBytes + kSegSmemBytes + size_t(c.warps_per_cta) * c.queries_per_warp * (size_t(1) << c.lane_bits) * 4;
 }
@@ -141,21 +145,23 @@ impir_status check_config(const impir_config& c, uint32_t words) {
         return fail(IMPIR_EINVAL, "queries_per_warp must be 1, 2, 4, 8 or 16");
     if (c.queries_per_warp * nk_for(words) > 16)
         return fail(IMPIR_EINVAL, "queries_per_warp %u too large for %u-byte records", c.queries_per_warp, words * 16);
-    if (c.warps_per_cta < 4 || c.warps_per_cta > 16) return fail(IMPIR_EINVAL, "warps_per_cta must be 4..16");
+    if (c.warps_per_cta < 4 || c.warps_per_cta > max_warps(c.queries_per_warp, words))
+        return fail(IMPIR_EINVAL, "warps_per_cta must be 4..%u for this record size and queries_per_warp",
+                    max_warps(c.queries_per_warp, words));
     if (c.queries_per_launch > 1) return fail(IMPIR_EINVAL, "queries_per_launch must be 0 or 1");
     if (smem_for(c) > kSmemMax) return fail(IMPIR_EINVAL, "configuration needs %zu bytes of shared memory", smem_for(c));
     return IMPIR_OK;
 }
 
 // Largest lane_bits that keeps enough warp tiles for every warp of the grid busy.
-impir_config default_config(uint64_t n_records, uint32_t words, uint32_t n_queries, int sms) {
+impir_config default_config_warps(uint64_t n_records, uint32_t words, uint32_t n_queries, int sms, uint32_t warps) {
     impir_config c{};
-    c.warps_per_cta = 16;
+    c.warps_per_cta = warps;
     c.queries_per_launch = 0;
     uint32_t qpw = 8;
     while (qpw > 1 && (qpw * nk_for(words) > 16 || qpw > n_queries)) qpw >>= 1;
     c.queries_per_warp = qpw;
-    const double warps = double(sms) * c.warps_per_cta;
+    const double all_warps = double(sms) * c.warps_per_cta;
     const double groups = std::ceil(double(n_queries) / qpw);
     c.lane_bits = 0;
     for (uint32_t s = kMaxLaneBits; s + 1 > 0; --s) {
@@ -163,13 +169,21 @@ impir_config default_config(uint64_t n_records, uint32_t words, uint32_t n_queri
         t.lane_bits = s;
         if (smem_for(t) > kSmemMax) continue;
         const double tiles = std::ceil(double(n_records) / double(32ull << s));
-        if (groups * tiles >= 3.0 * warps || s == 0) {
+        if (groups * tiles >= 3.0 * all_warps || s == 0) {
             c.lane_bits = s;
             break;
         }
     }
     if (c.lane_bits > 8) c.lane_bits = 8;
     return c;
+}
+
+// 20 warps per CTA where the kernel allows it and the lane subtrees stay as large as with 16.
+impir_config default_config(uint64_t n_records, uint32_t words, uint32_t n_queries, int sms) {
+    const impir_config c16 = default_config_warps(n_records, words, n_queries, sms, 16);
+    if (max_warps(c16.queries_per_warp, words) < 20) return c16;
+    const impir_config c20 = default_config_warps(n_records, words, n_queries, sms, 20);
+    return c20.lane_bits == c16.lane_bits && c20.queries_per_warp == c16.queries_per_warp ? c20 : c16;
 }
 
 impir_config config_for(const Db& db, uint32_t n_queries, int sms) {
@@ -231,6 +245,7 @@ uint32_t add_share_words(const impir_config& c) { return 32u << (c.lane_bits < 5
 
 impir_config add_config(impir_config c) {
     c.queries_per_warp = 1;
+    if (c.warps_per_cta > 16) c.warps_per_cta = 16;  // the additive kernels are built for 16 warps
     return c;
 }
 
@@ -683,10 +698,13 @@ impir_status impir_autotune(int32_t h, const uint8_t* d_keys, const uint32_t* d_
         for (int ds = -3; ds <= 2; ++ds) {
             const int s = int(base.lane_bits) + ds;
             if (s < 0 || s > int(kMaxLaneBits)) continue;
-            impir_config c = base;
-            c.queries_per_warp = qpw;
-            c.lane_bits = uint32_t(s);
-            if (check_config(c, db.stride / 16) == IMPIR_OK) cands.push_back(c);
+            for (uint32_t w : {16u, 20u}) {
+                impir_config c = base;
+                c.queries_per_warp = qpw;
+                c.lane_bits = uint32_t(s);
+                c.warps_per_cta = w;
+                if (check_config(c, db.stride / 16) == IMPIR_OK) cands.push_back(c);
+            }
         }
     }
     g_err.clear();

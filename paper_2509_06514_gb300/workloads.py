@@ -127,11 +127,11 @@ def single_query(seed: int = 0) -> Workload:
     return w
 
 
-def batched_256mib(seed: int = 1) -> Workload:
-    """Batched: N=2^20 x 256 B (256 MiB), 64 queries, domain 20 bits, one launch."""
+def batched_256mib(seed: int = 1, n_queries: int = 64) -> Workload:
+    """Batched: N=2^20 x 256 B (256 MiB), n_queries (64) queries, domain 20 bits, one launch."""
     rng = np.random.default_rng(seed)
-    w = Workload("batched: N=2^20 x 256 B, m=20, Q=64", 1 << 20, 256, seed)
-    w.batches.append(_batch(rng, 64, [20] * 64, w.n_records, seed + 1000, 0))
+    w = Workload(f"batched: N=2^20 x 256 B, m=20, Q={n_queries}", 1 << 20, 256, seed)
+    w.batches.append(_batch(rng, n_queries, [20] * n_queries, w.n_records, seed + 1000, 0))
     return w
 
 

@@ -69,6 +69,22 @@ def test_additive_chunked_lane_subtrees(built, orc, lane_bits, N, B):
         impir.impir_db_free(h)
 
 
+def test_additive_on_a_database_set_to_20_warps(built, orc):
+    """A launch shape of 20 warps per CTA (XOR answer) is narrowed to 16 for the additive one."""
+    N, B = 30000, 256
+    db = workloads.make_db(N, B, seed=2020)
+    rng = np.random.default_rng(2020)
+    keys = [random_key(rng, m, 0, i % 2) for i, m in enumerate([15, 15, 13])]
+    h = impir.impir_db_load(db, N, B)
+    try:
+        impir.impir_set_config(h, 7, 8, 20, 0)
+        got = impir.impir_answer_add32(h, b"".join(keys), len(keys), B)
+        for i, k in enumerate(keys):
+            assert got[i].tobytes() == orc.answer_add32(k, db, N, B), i
+    finally:
+        impir.impir_db_free(h)
+
+
 def test_additive_reconstruction_and_async(built, orc):
     import torch
     N, B, m = 20000, 64, 15

@@ -126,13 +126,13 @@ def test_batched_4gib_autotuned_and_graph(torch_cuda, orc):
 def test_uneven_8gib_batched_and_plain(torch_cuda, orc):
     """N=2^25 x 256 B (8 GiB), 1024 queries in batches of 1..512 mixing domains 2^23..2^25
     over DB prefixes, in the launch shape the benchmark times (lane_bits 7, 8 queries per warp,
-    16 warps, what its autotuner picks here); the library's default shape and the
+    20 warps, what its autotuner picks here); the library's default shape and the
     one-query-per-launch form give the same bits."""
     L = Loaded(torch_cuda, workloads.uneven_8gib())
     try:
         b, k0, _ = L.batches[0]
         dflt = L.answer_async(k0)
-        impir.impir_set_config(L.h, 7, 8, 16, 0)
+        impir.impir_set_config(L.h, 7, 8, 20, 0)
         sampled = {}
         for bi, (b, k0, k1) in enumerate(L.batches):
             r0 = L.answer_async(k0)
@@ -144,7 +144,7 @@ def test_uneven_8gib_batched_and_plain(torch_cuda, orc):
             if bi == 0:
                 assert np.array_equal(dflt, r0)
                 cfg = impir.impir_get_config(L.h, len(k0)).as_dict()
-                assert (cfg["lane_bits"], cfg["queries_per_warp"], cfg["warps_per_cta"]) == (7, 8, 16)
+                assert (cfg["lane_bits"], cfg["queries_per_warp"], cfg["warps_per_cta"]) == (7, 8, 20)
                 impir.impir_set_config(L.h, cfg["lane_bits"], 1, cfg["warps_per_cta"], 1)
                 p0 = L.answer_async(k0[:48])
                 impir.impir_set_config(L.h, cfg["lane_bits"], cfg["queries_per_warp"], cfg["warps_per_cta"], 0)

@@ -45,7 +45,9 @@ def test_undersized_workspace_and_bad_shapes(built):
         assert e.value.status == impir.IMPIR_ENOMEM
         for bad in (dict(lane_bits=11, queries_per_warp=1), dict(lane_bits=3, queries_per_warp=3),
                     dict(lane_bits=9, queries_per_warp=16), dict(lane_bits=3, queries_per_warp=2, warps_per_cta=2),
-                    dict(lane_bits=3, queries_per_warp=2, queries_per_launch=2)):
+                    dict(lane_bits=3, queries_per_warp=2, queries_per_launch=2),
+                    dict(lane_bits=3, queries_per_warp=2, warps_per_cta=21),
+                    dict(lane_bits=3, queries_per_warp=16, warps_per_cta=20)):
             with pytest.raises(impir.ImpirError) as e:
                 impir.impir_set_config(h, **bad)
             assert e.value.status == impir.IMPIR_EINVAL

@@ -71,6 +71,7 @@ def test_answer_matches_oracle(built, orc, prf, N, B, ms):
     dict(lane_bits=7, queries_per_warp=8), dict(lane_bits=9, queries_per_warp=2), dict(lane_bits=10, queries_per_warp=1),
     dict(lane_bits=4, queries_per_warp=4, queries_per_launch=1), dict(lane_bits=6, queries_per_warp=16),
     dict(lane_bits=2, queries_per_warp=16, warps_per_cta=4),
+    dict(lane_bits=7, queries_per_warp=8, warps_per_cta=20), dict(lane_bits=4, queries_per_warp=2, warps_per_cta=20),
 ])
 def test_every_launch_shape_matches_oracle(built, orc, cfg):
     N, B = 20000, 64
