@@ -175,3 +175,49 @@ def test_large_domains_over_small_database(built, orc, prf):
         assert bytes(got[5] ^ other[1]) == db[4999].tobytes()
     finally:
         impir.impir_db_free(dbh)
+
+
+@pytest.mark.parametrize("cfg", [None, dict(lane_bits=3, queries_per_warp=4)])
+def test_every_domain_size_in_one_batch(built, orc, cfg):
+    """One batch holding a key of every domain size 2^1 .. 2^40 (both PRFs, both parties):
+    40 groups and segments, domains far smaller and far larger than N."""
+    N, B = 3000, 24
+    db = workloads.make_db(N, B, seed=4141)
+    rng = np.random.default_rng(4141)
+    keys = []
+    for m in range(1, 41):
+        k = bytearray(random_key(rng, m, m % 2))
+        k[3] = (m // 2) % 2
+        keys.append(bytes(k))
+    order = rng.permutation(len(keys))
+    keys = [keys[i] for i in order]
+    dbh = impir.impir_db_load(db, N, B)
+    try:
+        if cfg:
+            impir.impir_set_config(dbh, **cfg)
+        got = gpu_answers(dbh, keys, B)
+        for i, k in enumerate(keys):
+            assert got[i].tobytes() == orc.answer_points(k, db, N, B), (i, k[2])
+    finally:
+        impir.impir_db_free(dbh)
+
+
+def test_large_batch_reconstructs(built, orc):
+    """12000 queries in one batch (domains 2^8 .. 2^13 over a 6000-record DB): every query's two
+    answers reconstruct its record, and a sample equals the oracle's answer."""
+    N, B = 6000, 16
+    db = workloads.make_db(N, B, seed=12000)
+    rng = np.random.default_rng(12000)
+    ms = [int(m) for m in rng.integers(8, 14, 12000)]
+    alphas = [int(rng.integers(0, min(N, 1 << m))) for m in ms]
+    pairs = [impir.dpf_gen(a, m, i % 2, rng.integers(0, 256, 32, dtype=np.uint8).tobytes())
+             for i, (a, m) in enumerate(zip(alphas, ms))]
+    dbh = impir.impir_db_load(db, N, B)
+    try:
+        r0 = gpu_answers(dbh, [p[0] for p in pairs], B)
+        r1 = gpu_answers(dbh, [p[1] for p in pairs], B)
+        assert np.array_equal(r0 ^ r1, db[alphas])
+        for i in rng.choice(len(pairs), 40, replace=False):
+            assert r0[i].tobytes() == orc.answer(pairs[i][0], db, N, B), i
+    finally:
+        impir.impir_db_free(dbh)
