@@ -574,20 +574,27 @@ __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_ba
 #pragma unroll
                 for (int q = 0; q < QC; ++q) sel[q] = bits[q * bw + (c0 >> 5)];
                 const uint32_t nloc = min(32u, nrec - c0);
-#pragma unroll 2
-                for (uint32_t i = 0; i < nloc; ++i) {
-                    uint4 v[NK];
-                    const uint4* rec = P.db + (tile_base - P.rec_lo + c0 + i) * W;
+                // RB records' loads in flight before their XORs (fewer for the widest records,
+                // whose loads already fill the registers)
+                constexpr int RB = NK <= 2 ? 4 : NK == 4 ? 2 : 1;
+                for (uint32_t i0 = 0; i0 < nloc; i0 += RB) {
+                    uint4 v[RB][NK];
 #pragma unroll
-                    for (int c = 0; c < NK; ++c) {
-                        const uint32_t k = k0 + lane + 32 * c;
-                        v[c] = k < W ? ld_db(rec + k) : make_uint4(0, 0, 0, 0);
+                    for (int u = 0; u < RB; ++u) {
+                        const uint4* rec = P.db + (tile_base - P.rec_lo + c0 + i0 + u) * W;
+#pragma unroll
+                        for (int c = 0; c < NK; ++c) {
+                            const uint32_t k = k0 + lane + 32 * c;
+                            v[u][c] = (k < W && i0 + u < nloc) ? ld_db(rec + k) : make_uint4(0, 0, 0, 0);
+                        }
                     }
 #pragma unroll
-                    for (int q = 0; q < QC; ++q)
-                        if ((sel[q] >> i) & 1u)
+                    for (int u = 0; u < RB; ++u)
 #pragma unroll
-                            for (int c = 0; c < NK; ++c) acc[q][c] = bxor4(acc[q][c], v[c]);
+                        for (int q = 0; q < QC; ++q)
+                            if ((sel[q] >> (i0 + u)) & 1u)
+#pragma unroll
+                                for (int c = 0; c < NK; ++c) acc[q][c] = bxor4(acc[q][c], v[u][c]);
                 }
             }
 #pragma unroll
