@@ -83,6 +83,37 @@ impir_status impir_db_free(int32_t db_handle);
 impir_status impir_db_info(int32_t db_handle, uint64_t* n_records, uint32_t* record_bytes, uint32_t* stride_bytes,
                            const void** d_records);
 
+/* ---- Row shards (a database split by rows across GPUs, the 1-D block layout of §3.3; the
+ * servers' per-shard results are combined like the partial results of Algorithm 1) ---- */
+
+/* Shard boundaries are multiples of this many records (so that no warp tile straddles two
+ * shards, whatever the launch shape). */
+#define IMPIR_SHARD_ALIGN 32768u
+
+/* Loads rows [row_lo, row_lo + n_rows) of a database of n_total records (host memory
+ * `records` holds just those rows, record_bytes each) into a new handle, like impir_db_load.
+ * Every answer on the handle (impir_answer, impir_answer_async, impir_answer_add32[_async],
+ * the server) is the partial answer over these rows only: a query with domain bits m covers
+ * global records [0, min(2^m, n_total)), of which this shard contributes the ones it holds.
+ * XOR of the shards' XOR answers (sum mod 2^32 of their additive answers), see
+ * impir_combine_partials, is the full answer. Bulk updates address rows relative to row_lo.
+ * EINVAL: row_lo not a multiple of IMPIR_SHARD_ALIGN, row_lo + n_rows beyond n_total, or an
+ * end that is neither n_total nor a multiple of IMPIR_SHARD_ALIGN; ENOMEM as impir_db_load. */
+impir_status impir_db_load_rows(const void* records, uint64_t n_rows, uint32_t record_bytes, uint64_t row_lo,
+                                uint64_t n_total, int32_t* db_handle);
+
+/* The row range of a handle: its first global row and the whole database's record count
+ * (0 and n_records for a handle that is not a shard). */
+impir_status impir_db_rows(int32_t db_handle, uint64_t* row_lo, uint64_t* n_total);
+
+/* Combines n_parts partial answers on the device: d_parts holds them back to back,
+ * part_bytes each (e.g. n_queries * record_bytes); d_out (part_bytes) receives their XOR
+ * (mode 0, the XOR answer) or their sum mod 2^32 word by word (mode 1, the additive answer;
+ * part_bytes a multiple of 4 and both pointers 4-byte aligned). Asynchronous on cuda_stream.
+ * d_out may not overlap d_parts. EINVAL: bad mode, sizes or alignment. */
+impir_status impir_combine_partials(int mode, const uint8_t* d_parts, uint32_t n_parts, uint64_t part_bytes,
+                                    uint8_t* d_out, void* cuda_stream);
+
 /* ---- Bulk updates (§3.3: a stable version answers queries while bulk updates are applied
  * in windows when the database is idle) ----
  * Records [first_record, first_record + n_records) are replaced by n_records records of

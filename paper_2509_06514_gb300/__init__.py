@@ -33,7 +33,7 @@ EXPORTS = [
     "impir_server_create", "impir_server_submit", "impir_server_take", "impir_server_stats", "impir_server_destroy",
     "impir_aes_calibrate", "impir_db_update", "impir_db_update_async", "impir_db_version", "impir_server_update",
     "impir_answer_streamed", "impir_answer_add32", "impir_answer_add32_async", "impir_tune_cache_save",
-    "impir_tune_cache_load",
+    "impir_tune_cache_load", "impir_db_load_rows", "impir_db_rows", "impir_combine_partials",
 ]
 
 
@@ -121,6 +121,11 @@ def lib():
                                                         ctypes.c_uint32, vp, vp]),
                 "impir_timing_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64),
                                                      ctypes.POINTER(ctypes.c_uint64)]),
+                "impir_db_load_rows": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
+                                                      ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32)]),
+                "impir_db_rows": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64),
+                                                 ctypes.POINTER(ctypes.c_uint64)]),
+                "impir_combine_partials": (ctypes.c_int, [ctypes.c_int, vp, ctypes.c_uint32, ctypes.c_uint64, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -184,6 +189,28 @@ def impir_db_attach(d_records, n_records: int, record_bytes: int, stride_bytes: 
 
 def impir_db_free(db: int) -> None:
     _check(lib().impir_db_free(db), "impir_db_free")
+
+
+def impir_db_load_rows(records, n_rows: int, record_bytes: int, row_lo: int, n_total: int) -> int:
+    """Row shard [row_lo, row_lo + n_rows) of an n_total-record database; `records` holds those rows."""
+    arr, p = _host(records)
+    assert arr.size >= n_rows * record_bytes
+    h = ctypes.c_int32(0)
+    _check(lib().impir_db_load_rows(p, n_rows, record_bytes, row_lo, n_total, ctypes.byref(h)), "impir_db_load_rows")
+    return h.value
+
+
+def impir_db_rows(db: int) -> tuple[int, int]:
+    """(row_lo, n_total) of a handle."""
+    lo, n = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().impir_db_rows(db, ctypes.byref(lo), ctypes.byref(n)), "impir_db_rows")
+    return lo.value, n.value
+
+
+def impir_combine_partials(mode: int, d_parts, n_parts: int, part_bytes: int, d_out, stream=None) -> None:
+    """d_out = XOR (mode 0) or sum mod 2^32 (mode 1) of n_parts back-to-back device parts."""
+    _check(lib().impir_combine_partials(mode, _dev(d_parts), n_parts, part_bytes, _dev(d_out), _stream(stream)),
+           "impir_combine_partials")
 
 
 def impir_db_info(db: int) -> dict:
@@ -306,6 +333,7 @@ def impir_device_sm_count() -> int:
 
 
 IMPIR_NOALLOC_SCRATCH_BYTES = 8 << 20
+IMPIR_SHARD_ALIGN = 32768
 
 
 def impir_server_create(max_batch: int, streams: int, max_record_bytes: int, accumulator_budget: int) -> int:

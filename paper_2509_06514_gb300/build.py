@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libimpir.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["fused_q1.cu", "fused_q2.cu", "fused_q4.cu", "fused_q8.cu", "fused_q16.cu", "fused_add.cu", "setup.cu", "noalloc.cu", "aes_bench.cu", "host_aes.cpp", "impir_host.cpp",
+UNITS = ["fused_q1.cu", "fused_q2.cu", "fused_q4.cu", "fused_q8.cu", "fused_q16.cu", "fused_add.cu", "setup.cu", "noalloc.cu", "aes_bench.cu", "combine.cu", "host_aes.cpp", "impir_host.cpp",
          "serve.cpp"]
 
 

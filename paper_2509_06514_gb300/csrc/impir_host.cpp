@@ -102,6 +102,8 @@ struct Db {
     bool cfg_set = false;
     impir_config cfg{};
     uint64_t version = 0;  // bumped by every bulk update
+    uint64_t row_lo = 0;   // a row shard: global index of its first row
+    uint64_t n_total = 0;  // and the whole database's record count (n for a whole database)
 };
 
 std::mutex g_db_mu;
@@ -276,16 +278,22 @@ impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_conf
                           const uint32_t* d_off, uint32_t n, uint8_t* d_out, uint8_t* d_ws, cudaStream_t st,
                           int mode = 0) {
     const WsLayout lay = ws_layout(n, db.stride);
+    // a row shard covers the warp tiles of its rows (shard bounds are whole tiles) of a
+    // database of n_total records; its device rows start at global row row_lo
+    const uint64_t T = 32ull << cfg.lane_bits;
+    const bool shard = db.row_lo != 0 || db.n_total != db.n;
     SetupParams sp{};
     sp.keys = d_keys;
     sp.key_off = d_off;
     sp.ws = d_ws;
     sp.lay = lay;
-    sp.n_records = db.n;
+    sp.n_records = db.n_total;
     sp.n_queries = n;
     sp.words = db.stride / 16;
     sp.lane_bits = cfg.lane_bits;
     sp.qpw = cfg.queries_per_warp;
+    sp.tile_lo = shard ? db.row_lo / T : 0;
+    sp.tile_hi = shard ? (db.row_lo + db.n + T - 1) / T : 0;
     CK(launch_setup(sp, st), "setup kernel launch");
 
     FusedParams fp{};
@@ -295,11 +303,12 @@ impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_conf
     fp.ws = d_ws;
     fp.te0 = dev.d_te0;
     fp.lay = lay;
-    fp.n_records = db.n;
+    fp.n_records = db.n_total;
     fp.n_queries = n;
     fp.words = db.stride / 16;
     fp.lane_bits = cfg.lane_bits;
     fp.bits_words = mode == 0 ? 1u << cfg.lane_bits : add_share_words(cfg);
+    fp.rec_lo = db.row_lo;
     std::memcpy(fp.mmo_rk, dev.mmo_rk, sizeof fp.mmo_rk);
     const size_t smem = mode == 0 ? smem_for(cfg) : smem_add(cfg);
     const bool timed = timing_on();
@@ -498,10 +507,38 @@ impir_status impir_db_load(const void* records, uint64_t n_records, uint32_t rec
     Db db;
     db.d = d;
     db.n = n_records;
+    db.n_total = n_records;
     db.bytes = record_bytes;
     db.stride = stride;
     db.owned = true;
     *db_handle = add_db(db);
+    return IMPIR_OK;
+}
+
+impir_status impir_db_load_rows(const void* records, uint64_t n_rows, uint32_t record_bytes, uint64_t row_lo,
+                                uint64_t n_total, int32_t* db_handle) {
+    if (!db_handle) return fail(IMPIR_EINVAL, "NULL argument");
+    if (n_total > (1ull << IMPIR_MAX_DOMAIN_BITS)) return fail(IMPIR_EINVAL, "more than 2^40 records");
+    if (n_rows == 0 || row_lo >= n_total || n_rows > n_total - row_lo)
+        return fail(IMPIR_EINVAL, "rows [%llu, +%llu) are not inside a database of %llu records",
+                    (unsigned long long)row_lo, (unsigned long long)n_rows, (unsigned long long)n_total);
+    if (row_lo % IMPIR_SHARD_ALIGN || (row_lo + n_rows != n_total && (row_lo + n_rows) % IMPIR_SHARD_ALIGN))
+        return fail(IMPIR_EINVAL, "shard bounds must be multiples of %u records (or the database end)",
+                    IMPIR_SHARD_ALIGN);
+    int32_t h = 0;
+    if (impir_status s = impir_db_load(records, n_rows, record_bytes, &h)) return s;
+    std::lock_guard<std::mutex> lk(g_db_mu);
+    g_dbs[h - 1].row_lo = row_lo;
+    g_dbs[h - 1].n_total = n_total;
+    *db_handle = h;
+    return IMPIR_OK;
+}
+
+impir_status impir_db_rows(int32_t h, uint64_t* row_lo, uint64_t* n_total) {
+    Db db;
+    if (impir_status s = get_db(h, &db)) return s;
+    if (row_lo) *row_lo = db.row_lo;
+    if (n_total) *n_total = db.n_total;
     return IMPIR_OK;
 }
 
@@ -515,6 +552,7 @@ impir_status impir_db_attach(const void* d_records, uint64_t n_records, uint32_t
     Db db;
     db.d = d_records;
     db.n = n_records;
+    db.n_total = n_records;
     db.bytes = record_bytes;
     db.stride = stride_bytes;
     db.owned = false;
