@@ -154,12 +154,17 @@ def aes_blocks(m: int) -> int:
 
 
 def kernel_source_hash() -> str:
-    """sha256 of the fused kernel's device source (a traffic capture is valid only for it)."""
+    """sha256 of the fused kernel's device code (a traffic capture is valid only for it): the
+    sources with comments removed and whitespace collapsed, so that editing a comment keeps it."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("fused.cuh", "fused_q1.cu", "fused_q2.cu", "fused_q4.cu", "fused_q8.cu", "setup.cu"):
-        with open(os.path.join(ROOT, "paper_2509_06514_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2509_06514_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()
 
 

@@ -8,16 +8,22 @@
 //   * Work unit = (warp tile, query group). A warp tile is 32 * 2^s consecutive leaves: lane l
 //     owns the perfect subtree of 2^s leaves rooted at depth m - s (the paper's worker
 //     subtrees, §3.2). A query group is up to QC queries of one domain size (§3.4 batching).
-//   * Each lane walks root -> its subtree root (the branch-parallel walk, one AES per level),
-//     then expands its subtree depth-first, two children per AES key schedule, and writes
-//     the 2^s selection bits of its leaves into shared memory. Selection bits never touch HBM.
-//   * The warp then reads the tile's records once (coalesced 16-byte loads) and XORs each
-//     record into the QC per-query accumulators held in registers (TaskletXOR), folds lanes
-//     with warp shuffles (MasterXOR), and XORs the result into the per-query answer in global
-//     memory with 64-bit atomic XOR (AggregateSubresults; XOR is order-independent, so the
-//     result is bit-exact whatever the order).
-//   * A persistent grid: warps take work units from a global counter, units ordered tile-major
-//     so that concurrently running warps read the same DB tile (served from L2).
+//   * The path root -> warp-tile root (the branch-parallel walk, one AES per level) is walked
+//     once per query of the group (lane q for query q); the warp then expands the five levels
+//     below it for the whole group together, so that every lane holds its subtree root for
+//     every query. Each lane expands its subtree depth-first, two children per AES key
+//     schedule, and writes the 2^s selection bits of its leaves into shared memory. Selection
+//     bits never touch HBM.
+//   * The warp then reads the tile's records once (coalesced 16-byte loads, several in flight
+//     per lane) and XORs each record into the QC per-query accumulators held in registers
+//     (TaskletXOR), folds lanes with warp shuffles (MasterXOR), and XORs the result into the
+//     per-query answer in global memory with 64-bit atomic XOR (AggregateSubresults; XOR is
+//     order-independent, so the result is bit-exact whatever the order).
+//   * MODE 1, the additive answer over Z_2^32: one query per unit, 32-bit shares instead of
+//     bits, scanned in chunks of 32 leaves per lane with integer multiply-adds.
+//   * A persistent grid, one CTA of 16 or 20 warps per SM: warps take work units from a global
+//     counter, units ordered tile-major so that concurrently running warps read the same DB
+//     tile (served from L2).
 //
 // AES: 32-bit T-tables (Te0..Te3) replicated per lane in shared memory. Row x of a 64 KiB
 // region holds [Te_a[x] for lanes 0..31 | Te_b[x] for lanes 0..31] (256 bytes), so the byte
