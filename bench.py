@@ -581,12 +581,8 @@ def main():
         s32 = (a0.view("<u4").astype(np.uint64) + a1.view("<u4").astype(np.uint64)) % (1 << 32)
         rec = s32.astype("<u4").view(np.uint8).reshape(len(sub), B)
         ok = sum(int(np.array_equal(rec[i], db[a])) for i, a in enumerate(al))
-        acfg = impir.impir_get_config(dbh, len(sub)).as_dict()
         additive = {"queries": len(sub), "add32_queries_per_s": len(sub) / t_add, "xor_queries_per_s": len(sub) / t_xor,
-                    "reconstructed_ok": ok,
-                    # the library narrows the additive launch to one query per warp and <= 16 warps
-                    "launch": {"lane_bits": acfg["lane_bits"], "queries_per_warp": 1,
-                               "warps_per_cta": min(acfg["warps_per_cta"], 16)}}
+                    "reconstructed_ok": ok, "launch": impir.impir_get_config_add32(dbh, len(sub)).as_dict()}
 
     # bulk update bandwidth: 256 MiB of new records into the resident DB (synchronous call)
     upd_n = min((256 << 20) // B, N // 2)

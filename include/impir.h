@@ -203,6 +203,11 @@ typedef struct {
 impir_status impir_get_config(int32_t db_handle, uint32_t n_queries, impir_config* cfg);
 impir_status impir_set_config(int32_t db_handle, const impir_config* cfg);
 
+/* The launch shape impir_answer_add32[_async] would use for a batch of n_queries keys on this
+ * database: the configuration set or tuned for it narrowed to the additive kernels (1 or 2
+ * queries per warp tile, at most 16 warps), else the additive default. */
+impir_status impir_get_config_add32(int32_t db_handle, uint32_t n_queries, impir_config* cfg);
+
 /* Times candidate configurations on the given asynchronous problem (same arguments as
  * impir_answer_async, which it runs repeatedly on cuda_stream), keeps the fastest for
  * this database, writes it to *best and records it in the process-wide tuning cache

@@ -34,6 +34,7 @@ EXPORTS = [
     "impir_aes_calibrate", "impir_db_update", "impir_db_update_async", "impir_db_version", "impir_server_update",
     "impir_answer_streamed", "impir_answer_add32", "impir_answer_add32_async", "impir_tune_cache_save",
     "impir_tune_cache_load", "impir_db_load_rows", "impir_db_rows", "impir_combine_partials",
+    "impir_get_config_add32",
 ]
 
 
@@ -91,6 +92,7 @@ def lib():
                 "impir_workspace_status": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_uint32),
                                                           ctypes.POINTER(ctypes.c_uint32)]),
                 "impir_get_config": (ctypes.c_int, [ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(impir_config)]),
+                "impir_get_config_add32": (ctypes.c_int, [ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(impir_config)]),
                 "impir_set_config": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(impir_config)]),
                 "impir_autotune": (ctypes.c_int, [ctypes.c_int32, vp, vp, ctypes.c_uint32, vp, vp, ctypes.c_size_t,
                                                   vp, ctypes.POINTER(impir_config)]),
@@ -289,6 +291,13 @@ def impir_workspace_status(d_workspace) -> tuple[int, int]:
 def impir_get_config(db: int, n_queries: int = 1) -> impir_config:
     c = impir_config()
     _check(lib().impir_get_config(db, n_queries, ctypes.byref(c)), "impir_get_config")
+    return c
+
+
+def impir_get_config_add32(db: int, n_queries: int = 1) -> impir_config:
+    """The launch shape of the additive answer for a batch of n_queries on this database."""
+    c = impir_config()
+    _check(lib().impir_get_config_add32(db, n_queries, ctypes.byref(c)), "impir_get_config_add32")
     return c
 
 

@@ -19,8 +19,9 @@
 //     (TaskletXOR), folds lanes with warp shuffles (MasterXOR), and XORs the result into the
 //     per-query answer in global memory with 64-bit atomic XOR (AggregateSubresults; XOR is
 //     order-independent, so the result is bit-exact whatever the order).
-//   * MODE 1, the additive answer over Z_2^32: one query per unit, 32-bit shares instead of
-//     bits, scanned in chunks of 32 leaves per lane with integer multiply-adds.
+//   * MODE 1, the additive answer over Z_2^32: one or two queries per unit, 32-bit shares
+//     instead of bits, the queries' walks advanced in turn by chunks of leaves and each chunk's
+//     records scanned once for all of them with integer multiply-adds.
 //   * A persistent grid, one CTA of 16 or 20 warps per SM: warps take work units from a global
 //     counter, units ordered tile-major so that concurrently running warps read the same DB
 //     tile (served from L2).
@@ -301,58 +302,75 @@ __device__ __forceinline__ void red_add(uint4* dst, const uint4 v) {
     if (v.w) atomicAdd(d + 3, v.w);
 }
 
-// Additive answer of one chunk of a warp tile for one query: acc += share * D[r], word by word
-// mod 2^32 (records read as little-endian 32-bit words), added into the query's accumulator.
-// The chunk holds `runs` runs of `run_len` consecutive records; run l starts at tile record
-// (l << sq) + chunk_off and its shares sit at vals[l * run_len ...]. Records at or past `nrec`
-// (the DB end) are skipped; runs start in ascending order.
-template <int NK>
+// Additive answer of one chunk of a warp tile for the unit's queries: acc_q += share_q * D[r],
+// word by word mod 2^32 (records read as little-endian 32-bit words), added into each query's
+// accumulator; every record is loaded once for all the queries. The chunk holds `runs` runs of
+// `run_len` consecutive records; run l starts at tile record (l << sq) + chunk_off and query
+// q's shares of it sit at vals[q * qstride + l * run_len ...]. Records at or past `nrec` (the
+// DB end) are skipped; runs start in ascending order.
+template <int QC, int NK>
 __device__ __forceinline__ void scan_chunk_add(const FusedParams& P, uint64_t tile_base, uint32_t nrec,
-                                               const uint32_t* vals, uint32_t runs, uint32_t run_len, uint32_t sq,
-                                               uint32_t chunk_off, uint32_t qdst, uint4* acc_out, uint32_t lane) {
+                                               const uint32_t* vals, uint32_t qstride, uint32_t count,
+                                               const uint32_t* qidx, uint32_t runs, uint32_t run_len, uint32_t sq,
+                                               uint32_t chunk_off, uint4* acc_out, uint32_t lane) {
     const uint32_t W = P.words;
     const uint4* tile = P.db + (tile_base - P.rec_lo) * W;
     if constexpr (NK == 1) {
         // W <= 32: R records per step, lane -> (record lr, word lk)
         const uint32_t R = 32u / W, lr = lane / W, lk = lane - lr * W;
         const bool on = lr < R;
-        uint4 acc = make_uint4(0, 0, 0, 0);
+        uint4 acc[QC];
+#pragma unroll
+        for (int q = 0; q < QC; ++q) acc[q] = make_uint4(0, 0, 0, 0);
+        constexpr int RB = QC == 1 ? 8 : 4;  // records' loads in flight per lane (fewer with more accumulators)
         for (uint32_t l = 0; l < runs; ++l) {
             const uint32_t rb = (l << sq) + chunk_off;
             if (rb >= nrec) break;
             const uint32_t n = min(run_len, nrec - rb);
             const uint32_t* vl = vals + l * run_len;
             const uint4* bl = tile + size_t(rb) * W + lk;
-            // eight records' loads in flight per lane before their multiply-adds: the scan
-            // streams the tile from L2 and has little arithmetic per load to hide latency behind
-            for (uint32_t r0 = 0; r0 < n; r0 += 8 * R) {
-                uint4 v[8];
-                uint32_t sv[8];
+            for (uint32_t r0 = 0; r0 < n; r0 += RB * R) {
+                uint4 v[RB];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
+                for (int u = 0; u < RB; ++u) {
                     const uint32_t r = r0 + u * R + lr;
-                    const bool ok = on && r < n;
-                    v[u] = ok ? ld_db(bl + size_t(r) * W) : make_uint4(0, 0, 0, 0);
-                    sv[u] = ok ? vl[r] : 0u;
+                    v[u] = (on && r < n) ? ld_db(bl + size_t(r) * W) : make_uint4(0, 0, 0, 0);
                 }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) mad4(acc, v[u], sv[u]);
+                for (int u = 0; u < RB; ++u) {
+                    const uint32_t r = r0 + u * R + lr;
+                    if (on && r < n)
+#pragma unroll
+                        for (int q = 0; q < QC; ++q)
+                            if (uint32_t(q) < count) mad4(acc[q], v[u], vl[q * qstride + r]);
+                }
             }
         }
         if (R * W == 32) {
             for (uint32_t off = W; off < 32; off <<= 1)
-                acc = add4(acc, make_uint4(__shfl_xor_sync(0xffffffffu, acc.x, off), __shfl_xor_sync(0xffffffffu, acc.y, off),
-                                           __shfl_xor_sync(0xffffffffu, acc.z, off), __shfl_xor_sync(0xffffffffu, acc.w, off)));
-            if (lr == 0) red_add(acc_out + size_t(qdst) * W + lk, acc);
+#pragma unroll
+                for (int q = 0; q < QC; ++q)
+                    acc[q] = add4(acc[q], make_uint4(__shfl_xor_sync(0xffffffffu, acc[q].x, off),
+                                                     __shfl_xor_sync(0xffffffffu, acc[q].y, off),
+                                                     __shfl_xor_sync(0xffffffffu, acc[q].z, off),
+                                                     __shfl_xor_sync(0xffffffffu, acc[q].w, off)));
+            if (lr == 0)
+#pragma unroll
+                for (int q = 0; q < QC; ++q)
+                    if (uint32_t(q) < count) red_add(acc_out + size_t(qidx[q]) * W + lk, acc[q]);
         } else if (on) {
-            red_add(acc_out + size_t(qdst) * W + lk, acc);
+#pragma unroll
+            for (int q = 0; q < QC; ++q)
+                if (uint32_t(q) < count) red_add(acc_out + size_t(qidx[q]) * W + lk, acc[q]);
         }
     } else {
         // W > 32: the whole warp reads one record per step, NK words per lane, in column passes
         for (uint32_t k0 = 0; k0 < W; k0 += 32 * NK) {
-            uint4 acc[NK];
+            uint4 acc[QC][NK];
 #pragma unroll
-            for (int c = 0; c < NK; ++c) acc[c] = make_uint4(0, 0, 0, 0);
+            for (int q = 0; q < QC; ++q)
+#pragma unroll
+                for (int c = 0; c < NK; ++c) acc[q][c] = make_uint4(0, 0, 0, 0);
             for (uint32_t l = 0; l < runs; ++l) {
                 const uint32_t rb = (l << sq) + chunk_off;
                 if (rb >= nrec) break;
@@ -360,20 +378,30 @@ __device__ __forceinline__ void scan_chunk_add(const FusedParams& P, uint64_t ti
                 const uint32_t* vl = vals + l * run_len;
 #pragma unroll 4
                 for (uint32_t r = 0; r < n; ++r) {
-                    const uint32_t sv = vl[r];
                     const uint4* rec = tile + size_t(rb + r) * W;
+                    uint4 v[NK];
 #pragma unroll
                     for (int c = 0; c < NK; ++c) {
                         const uint32_t k = k0 + lane + 32 * c;
-                        if (k < W) mad4(acc[c], ld_db(rec + k), sv);
+                        v[c] = k < W ? ld_db(rec + k) : make_uint4(0, 0, 0, 0);
                     }
+#pragma unroll
+                    for (int q = 0; q < QC; ++q)
+                        if (uint32_t(q) < count) {
+                            const uint32_t sv = vl[q * qstride + r];
+#pragma unroll
+                            for (int c = 0; c < NK; ++c) mad4(acc[q][c], v[c], sv);
+                        }
                 }
             }
 #pragma unroll
-            for (int c = 0; c < NK; ++c) {
-                const uint32_t k = k0 + lane + 32 * c;
-                if (k < W) red_add(acc_out + size_t(qdst) * W + k, acc[c]);
-            }
+            for (int q = 0; q < QC; ++q)
+                if (uint32_t(q) < count)
+#pragma unroll
+                    for (int c = 0; c < NK; ++c) {
+                        const uint32_t k = k0 + lane + 32 * c;
+                        if (k < W) red_add(acc_out + size_t(qidx[q]) * W + k, acc[q][c]);
+                    }
         }
     }
 }
@@ -381,18 +409,11 @@ __device__ __forceinline__ void scan_chunk_add(const FusedParams& P, uint64_t ti
 // Selection bits of lane's subtree: root -> depth D walk (Eq. (3) one edge per level), then
 // a depth-first expansion down to the leaves at depth m; bit r of `bits` (relative to the
 // warp tile) is lsb(R(m, tile_first_leaf + r)).
-// MODE 0 writes selection bits. MODE 1 (the additive answer) computes one 32-bit share per
-// leaf, (-1)^party low32(R(m, j)), into a buffer of 32 leaves per lane (one chunk), and the
-// warp scans the chunk's records whenever the buffer is full: lane subtrees can be larger than
-// the buffer, and in MODE 1 every lane of the warp must call this function (lanes past the DB
-// end walk nodes that exist in the tree; the scan skips their records).
 // The walk starts from `start`, the node at depth d0 on the lane's path (the root with d0 = 0,
 // or the warp-tile root the warp computed once for this query).
-template <int PRF, int MODE, int NK = 1>
-__device__ __forceinline__ void lane_eval(const FusedParams& P, const uint8_t* kq, uint32_t m, uint32_t D,
-                                          uint64_t sub, uint32_t sq, uint32_t* bits, uint32_t lane, uint32_t L,
-                                          const Blk start, uint32_t d0, uint64_t tile_base = 0, uint32_t nrec = 0,
-                                          uint32_t qdst = 0, uint4* acc_out = nullptr) {
+template <int PRF>
+__device__ __forceinline__ Blk walk_down(const FusedParams& P, const uint8_t* kq, uint32_t m, uint32_t D, uint64_t sub,
+                                         uint32_t L, const Blk start, uint32_t d0) {
     Blk node = start;
     for (uint32_t d = d0 + 1; d <= D; ++d) {
         const uint32_t x = uint32_t(sub >> (D - d)) & 1u;
@@ -401,47 +422,24 @@ __device__ __forceinline__ void lane_eval(const FusedParams& P, const uint8_t* k
         const Blk f = PRF == 0 ? keyed_one(node, x, L) : mmo_one(node, x, L, P.mmo_rk);
         node = bxor(f, c);
     }
-    const uint32_t neg = kq[3] ? 0xffffffffu : 0u;  // party 1 negates its shares (mod 2^32)
+    return node;
+}
+
+template <int PRF>
+__device__ __forceinline__ void lane_eval(const FusedParams& P, const uint8_t* kq, uint32_t m, uint32_t D,
+                                          uint64_t sub, uint32_t sq, uint32_t* bits, uint32_t lane, uint32_t L,
+                                          const Blk start, uint32_t d0) {
+    Blk node = walk_down<PRF>(P, kq, m, D, sub, L, start, d0);
     if (sq == 0) {
-        if (MODE == 0) {
-            atomicOr(&bits[lane >> 5], (node.x & 1u) << (lane & 31));
-        } else {
-            bits[lane] = (node.x ^ neg) - neg;
-            __syncwarp();
-            scan_chunk_add<NK>(P, tile_base, nrec, bits, 1, 32, 0, 0, qdst, acc_out, lane);
-        }
+        atomicOr(&bits[lane >> 5], (node.x & 1u) << (lane & 31));
         return;
     }
-    // MODE 1 chunks: ch leaves per lane; with lane subtrees of at most 32 leaves the chunk is
-    // the whole tile (one run of consecutive records), else 32 runs of 32 records
-    const uint32_t ch_bits = sq < 5 ? sq : 5u, ch = 1u << ch_bits;
-    const uint32_t runs = sq > 5 ? 32u : 1u, run_len = sq > 5 ? 32u : (32u << sq);
     Blk stk[kMaxLaneBits];
     uint32_t depth = D, p = 0, acc = 0;
     const uint32_t npairs = 1u << (sq - 1);
     for (;;) {
         const uint32_t t = node.x & 1u;
-        if (depth == m - 1 && MODE == 1) {
-            uint32_t wa, wb;
-            if (PRF == 0)
-                keyed_leaf_words(node, L, wa, wb);
-            else
-                mmo_leaf_words(node, L, P.mmo_rk, wa, wb);
-            wa ^= cw_load(kq, m, t, 0, m).x;
-            wb ^= cw_load(kq, m, t, 1, m).x;
-            const uint32_t o = (2 * p) & (ch - 1), r = (lane << ch_bits) + o;
-            bits[r] = (wa ^ neg) - neg;
-            bits[r + 1] = (wb ^ neg) - neg;
-            if (o + 2 == ch) {  // chunk full: scan its records (all lanes arrive here together)
-                __syncwarp();
-                scan_chunk_add<NK>(P, tile_base, nrec, bits, runs, run_len, sq, 2 * p + 2 - ch, qdst, acc_out, lane);
-                __syncwarp();
-            }
-            ++p;
-            if (p == npairs) break;
-            depth = m - 1 - (__ffs(int(p)) - 1);
-            node = stk[depth - D];
-        } else if (depth == m - 1) {
+        if (depth == m - 1) {
             uint32_t b2 = PRF == 0 ? keyed_leaf_bits(node, L) : mmo_leaf_bits(node, L, P.mmo_rk);
             b2 ^= cw_lsb(kq, m, t, 0, m) | (cw_lsb(kq, m, t, 1, m) << 1);
             acc |= b2 << ((2 * p) & 31);
@@ -466,7 +464,120 @@ __device__ __forceinline__ void lane_eval(const FusedParams& P, const uint8_t* k
             node = a;
         }
     }
-    if (MODE == 0 && sq < 5) atomicOr(&bits[(lane << sq) >> 5], acc << ((lane << sq) & 31));
+    if (sq < 5) atomicOr(&bits[(lane << sq) >> 5], acc << ((lane << sq) & 31));
+}
+
+// ---- additive answer (MODE 1) ----
+
+// A lane's depth-first walk of one query's subtree, resumable after every chunk of leaves so
+// that the warp can advance several queries' walks between two scans.
+struct AddWalk {
+    Blk node;               // the next node to expand
+    uint32_t depth, p;      // its depth; leaf pairs written so far
+    Blk stk[kMaxLaneBits];  // pending right children, by depth - D
+};
+
+// Advances the walk by ch leaves (ch >= 2, even): the shares (-1)^party low32(R(m, j)) of the
+// lane's next ch leaves go to shares[lane * ch + 0 .. ch - 1].
+template <int PRF>
+__device__ __forceinline__ void add_walk_chunk(const FusedParams& P, const uint8_t* kq, uint32_t m, uint32_t D,
+                                               uint32_t sq, AddWalk& w, uint32_t ch, uint32_t* shares, uint32_t lane,
+                                               uint32_t L, uint32_t neg) {
+    Blk node = w.node;
+    uint32_t depth = w.depth, p = w.p;
+    const uint32_t npairs = 1u << (sq - 1), end = p + ch / 2;
+    for (;;) {
+        const uint32_t t = node.x & 1u;
+        if (depth == m - 1) {
+            uint32_t wa, wb;
+            if (PRF == 0)
+                keyed_leaf_words(node, L, wa, wb);
+            else
+                mmo_leaf_words(node, L, P.mmo_rk, wa, wb);
+            wa ^= cw_load(kq, m, t, 0, m).x;
+            wb ^= cw_load(kq, m, t, 1, m).x;
+            const uint32_t r = lane * ch + ((2 * p) & (ch - 1));
+            shares[r] = (wa ^ neg) - neg;
+            shares[r + 1] = (wb ^ neg) - neg;
+            ++p;
+            if (p == npairs) break;
+            depth = m - 1 - (__ffs(int(p)) - 1);
+            node = w.stk[depth - D];
+            if (p == end) break;
+        } else {
+            const Blk c0 = cw_load(kq, m, t, 0, depth + 1);
+            const Blk c1 = cw_load(kq, m, t, 1, depth + 1);
+            Blk a, b;
+            if (PRF == 0)
+                keyed_pair(node, L, c0, c1, a, b);
+            else
+                mmo_pair(node, L, P.mmo_rk, c0, c1, a, b);
+            ++depth;
+            w.stk[depth - D] = b;
+            node = a;
+        }
+    }
+    w.node = node;
+    w.depth = depth;
+    w.p = p;
+}
+
+// One work unit of the additive answer: the group's queries over one warp tile. Every lane
+// walks from the warp-tile root (`top`, held by lane q for query q) to its subtree root for
+// each query, then the warp alternates: each query's walk advances by one chunk of ch leaves
+// per lane (ch = 32 / QC, so the group's shares fill 4 KiB per warp), and the chunk's records
+// are scanned once for all the queries. Lanes past the DB end walk nodes that exist in the
+// tree; the scan skips their records. All 32 lanes take part (the scan is warp-wide).
+template <int QC, int NK>
+__device__ __forceinline__ void unit_add(const FusedParams& P, const GroupDesc& gd, const uint32_t* qidx,
+                                         uint64_t tile_base, uint32_t nrec, uint64_t sub, uint32_t sq, uint32_t D,
+                                         uint32_t Dt, const Blk top, uint32_t* shares, uint4* acc_out, uint32_t lane,
+                                         uint32_t L) {
+    const uint32_t m = gd.m, count = gd.count;
+    AddWalk w[QC];
+    uint32_t neg[QC];
+    const uint32_t ch = sq == 0 ? 1u : min(1u << sq, 32u / QC), qstride = 32 * ch;
+#pragma unroll
+    for (int q = 0; q < QC; ++q) {
+        neg[q] = 0;
+        if (uint32_t(q) < count) {
+            const uint8_t* kq = P.keys + P.key_off[qidx[q]];
+            const Blk start{__shfl_sync(0xffffffffu, top.x, q), __shfl_sync(0xffffffffu, top.y, q),
+                            __shfl_sync(0xffffffffu, top.z, q), __shfl_sync(0xffffffffu, top.w, q)};
+            w[q].node = kq[1] == 0 ? walk_down<0>(P, kq, m, D, sub, L, start, Dt)
+                                   : walk_down<1>(P, kq, m, D, sub, L, start, Dt);
+            w[q].depth = D;
+            w[q].p = 0;
+            neg[q] = kq[3] ? 0xffffffffu : 0u;  // party 1 negates its shares (mod 2^32)
+        }
+    }
+    if (sq == 0) {  // one leaf per lane: the subtree root is the leaf
+#pragma unroll
+        for (int q = 0; q < QC; ++q)
+            if (uint32_t(q) < count) shares[q * qstride + lane] = (w[q].node.x ^ neg[q]) - neg[q];
+        __syncwarp();
+        scan_chunk_add<QC, NK>(P, tile_base, nrec, shares, qstride, count, qidx, 1, 32, 0, 0, acc_out, lane);
+        return;
+    }
+    // with lane subtrees of at most ch leaves the chunk is the whole tile (one run of
+    // consecutive records), else 32 runs of ch records
+    const uint32_t runs = (1u << sq) > ch ? 32u : 1u, run_len = runs == 32 ? ch : (32u << sq);
+    const uint32_t nchunks = (1u << sq) / ch;
+    for (uint32_t c = 0; c < nchunks; ++c) {
+#pragma unroll
+        for (int q = 0; q < QC; ++q)
+            if (uint32_t(q) < count) {
+                const uint8_t* kq = P.keys + P.key_off[qidx[q]];
+                if (kq[1] == 0)
+                    add_walk_chunk<0>(P, kq, m, D, sq, w[q], ch, shares + q * qstride, lane, L, neg[q]);
+                else
+                    add_walk_chunk<1>(P, kq, m, D, sq, w[q], ch, shares + q * qstride, lane, L, neg[q]);
+            }
+        __syncwarp();
+        scan_chunk_add<QC, NK>(P, tile_base, nrec, shares, qstride, count, qidx, runs, run_len, sq, c * ch, acc_out,
+                               lane);
+        __syncwarp();
+    }
 }
 
 __device__ __forceinline__ void red_xor(uint4* dst, const uint4 v) {
@@ -622,7 +733,7 @@ template <int QC, int NK, int MODE = 0>
 // per warp, which fit in 102 registers; 512 for the others, which need more.
 __global__ void __launch_bounds__((MODE == 0 && NK == 1 && QC <= 8) ? 640 : 512, 1)
     fused_kernel(const __grid_constant__ FusedParams P) {
-    static_assert(MODE == 0 || QC == 1, "the additive answer evaluates one query per warp tile");
+    static_assert(MODE == 0 || QC * NK <= 8, "additive accumulators: at most 8 uint4 per lane");
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
     const uint32_t lane = tid & 31, warp = tid >> 5;
 
@@ -701,6 +812,11 @@ __global__ void __launch_bounds__((MODE == 0 && NK == 1 && QC <= 8) ? 640 : 512,
                 top = bxor(f, cw_load(kq, m, top.x & 1u, x, d));
             }
         }
+        if constexpr (MODE == 1) {
+            unit_add<QC, NK>(P, gd, qidx, tile_base, nrec, sub, sq, D, Dt, top, bits, acc_out, lane, L);
+            __syncwarp();
+            continue;
+        }
         if (coop) {
             uint8_t* nodes = reinterpret_cast<uint8_t*>(bits);  // query q's nodes at q * slot
             const uint32_t slot = P.bits_words * 4;
@@ -744,9 +860,9 @@ __global__ void __launch_bounds__((MODE == 0 && NK == 1 && QC <= 8) ? 640 : 512,
                 const Blk start{pv.x, pv.y, pv.z, pv.w};
                 if (lane_on) {
                     if (prf == 0)
-                        lane_eval<0, MODE>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, D - 1);
+                        lane_eval<0>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, D - 1);
                     else
-                        lane_eval<1, MODE>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, D - 1);
+                        lane_eval<1>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, D - 1);
                 }
             }
         } else {
@@ -755,18 +871,16 @@ __global__ void __launch_bounds__((MODE == 0 && NK == 1 && QC <= 8) ? 640 : 512,
                 const uint32_t prf = kq[1];
                 const Blk start{__shfl_sync(0xffffffffu, top.x, qi), __shfl_sync(0xffffffffu, top.y, qi),
                                 __shfl_sync(0xffffffffu, top.z, qi), __shfl_sync(0xffffffffu, top.w, qi)};
-                if (MODE == 1 || lane_on) {  // MODE 1 scans inside the walk: the whole warp takes part
+                if (lane_on) {
                     if (prf == 0)
-                        lane_eval<0, MODE, NK>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, Dt,
-                                               tile_base, nrec, qidx[qi], acc_out);
+                        lane_eval<0>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, Dt);
                     else
-                        lane_eval<1, MODE, NK>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, Dt,
-                                               tile_base, nrec, qidx[qi], acc_out);
+                        lane_eval<1>(P, kq, m, D, sub, sq, bits + qi * P.bits_words, lane, L, start, Dt);
                 }
             }
         }
         __syncwarp();
-        if constexpr (MODE == 0) scan_tile<QC, NK>(P, tile_base, nrec, bits, gd.count, qidx, acc_out, lane);
+        scan_tile<QC, NK>(P, tile_base, nrec, bits, gd.count, qidx, acc_out, lane);
         __syncwarp();
     }
 }

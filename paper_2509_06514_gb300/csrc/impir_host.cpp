@@ -140,7 +140,10 @@ size_t smem_for(const impir_config& c) {
 
 constexpr size_t kSmemMax = 227 * 1024;
 
-impir_status check_config(const impir_config& c, uint32_t words) {
+size_t smem_add(const impir_config& c);
+
+// mode 0: the XOR answer's kernels; mode 1: the additive answer's (after add_config)
+impir_status check_config(const impir_config& c, uint32_t words, int mode = 0) {
     if (c.lane_bits > kMaxLaneBits) return fail(IMPIR_EINVAL, "lane_bits %u > %u", c.lane_bits, kMaxLaneBits);
     if (c.queries_per_warp != 1 && c.queries_per_warp != 2 && c.queries_per_warp != 4 && c.queries_per_warp != 8 &&
         c.queries_per_warp != 16)
@@ -151,7 +154,8 @@ impir_status check_config(const impir_config& c, uint32_t words) {
         return fail(IMPIR_EINVAL, "warps_per_cta must be 4..%u for this record size and queries_per_warp",
                     max_warps(c.queries_per_warp, words));
     if (c.queries_per_launch > 1) return fail(IMPIR_EINVAL, "queries_per_launch must be 0 or 1");
-    if (smem_for(c) > kSmemMax) return fail(IMPIR_EINVAL, "configuration needs %zu bytes of shared memory", smem_for(c));
+    const size_t smem = mode == 0 ? smem_for(c) : smem_add(c);
+    if (smem > kSmemMax) return fail(IMPIR_EINVAL, "configuration needs %zu bytes of shared memory", smem);
     return IMPIR_OK;
 }
 
@@ -241,28 +245,39 @@ void count_launches(uint64_t n) {
 // ---- launches ----
 // Launch shape of the additive answer derived from a configuration: one query per warp tile
 // and a lane subtree small enough for one 32-bit share per leaf in shared memory.
-// The additive answer keeps one 32-bit share per leaf for at most 32 leaves per lane at a time
-// (larger lane subtrees are scanned in chunks), one query per warp tile.
-uint32_t add_share_words(const impir_config& c) { return 32u << (c.lane_bits < 5 ? c.lane_bits : 5u); }
+// The additive answer takes 1 or 2 queries per warp tile (records up to 2 KiB: 2, else 1; with
+// 4 the extra walk states and smaller chunks cost more than the shared record loads save), and
+// keeps one 32-bit share per leaf for 32 / queries leaves per lane at a time and query (larger
+// lane subtrees are scanned in chunks): 4 KiB per warp.
+uint32_t max_add_qpw(uint32_t words) { return nk_for(words) <= 4 ? 2u : 1u; }
 
-impir_config add_config(impir_config c) {
-    c.queries_per_warp = 1;
+// 32-bit share words per query slot of a warp.
+uint32_t add_share_words(const impir_config& c) {
+    const uint32_t ch = std::min(1u << c.lane_bits, 32u / c.queries_per_warp);
+    return 32u * ch;
+}
+
+impir_config add_config(impir_config c, uint32_t words) {
+    c.queries_per_warp = std::min(c.queries_per_warp, max_add_qpw(words));
     if (c.warps_per_cta > 16) c.warps_per_cta = 16;  // the additive kernels are built for 16 warps
     return c;
 }
 
-// Default shape of the additive answer (one query per unit): the largest lane subtree, up to
-// 256 leaves, that still leaves three units per resident warp.
-impir_config default_add_config(uint64_t n_records, uint32_t n_queries, int sms) {
+// Default shape of the additive answer: as many queries per unit as the record size allows
+// (up to 2, and no more than the batch), and the largest lane subtree, up to 256 leaves, that
+// still leaves three units per resident warp.
+impir_config default_add_config(uint64_t n_records, uint32_t words, uint32_t n_queries, int sms) {
     impir_config c{};
     c.warps_per_cta = 16;
-    c.queries_per_warp = 1;
+    c.queries_per_warp = max_add_qpw(words);
+    while (c.queries_per_warp > 1 && c.queries_per_warp > n_queries) c.queries_per_warp >>= 1;
     c.queries_per_launch = 0;
     const double warps = double(sms) * c.warps_per_cta;
+    const double groups = std::ceil(double(n_queries) / c.queries_per_warp);
     c.lane_bits = 0;
     for (uint32_t s = 8; s > 0; --s) {
         const double tiles = std::ceil(double(n_records) / double(32ull << s));
-        if (double(n_queries) * tiles >= 3.0 * warps) {
+        if (groups * tiles >= 3.0 * warps) {
             c.lane_bits = s;
             break;
         }
@@ -271,7 +286,7 @@ impir_config default_add_config(uint64_t n_records, uint32_t n_queries, int sms)
 }
 
 size_t smem_add(const impir_config& c) {
-    return kTableBytes + kSegSmemBytes + size_t(c.warps_per_cta) * add_share_words(c) * 4;
+    return kTableBytes + kSegSmemBytes + size_t(c.warps_per_cta) * c.queries_per_warp * add_share_words(c) * 4;
 }
 
 impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_config& cfg, const uint8_t* d_keys,
@@ -322,7 +337,8 @@ impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_conf
         CK(launch_fused(cfg.queries_per_warp, nk_for(fp.words), dim3(dev.sms), dim3(cfg.warps_per_cta * 32), smem, st, fp),
            "fused kernel launch");
     else
-        CK(launch_fused_add(nk_for(fp.words), dim3(dev.sms), dim3(cfg.warps_per_cta * 32), smem, st, fp),
+        CK(launch_fused_add(cfg.queries_per_warp, nk_for(fp.words), dim3(dev.sms), dim3(cfg.warps_per_cta * 32), smem,
+                            st, fp),
            "fused kernel launch (additive)");
     if (timed) {
         CK(cudaEventRecord(ev1, st), "event record");
@@ -351,13 +367,13 @@ impir_status answer_async_impl(const Db& db, const impir_config* cfg_in, const u
     if (!d_keys || !d_off || !d_out || !d_ws) return fail(IMPIR_EINVAL, "NULL device buffer");
     if (reinterpret_cast<uintptr_t>(d_ws) & 255) return fail(IMPIR_EINVAL, "workspace must be 256-byte aligned");
     impir_config cfg = cfg_in                      ? *cfg_in
-                       : (mode == 1 && !db.cfg_set) ? default_add_config(db.n, n, dev->sms)
+                       : (mode == 1 && !db.cfg_set) ? default_add_config(db.n, db.stride / 16, n, dev->sms)
                                                     : config_for(db, n, dev->sms);
     if (mode == 1) {
         if (db.bytes % 4) return fail(IMPIR_EINVAL, "the additive answer needs records of a multiple of 4 bytes");
-        cfg = add_config(cfg);
+        cfg = add_config(cfg, db.stride / 16);
     }
-    if (impir_status s = check_config(cfg, db.stride / 16)) return s;
+    if (impir_status s = check_config(cfg, db.stride / 16, mode)) return s;
     if (cfg.queries_per_launch == 1) {
         if (ws_bytes < ws_layout(1, db.stride).total) return fail(IMPIR_ENOMEM, "workspace too small");
         for (uint32_t q = 0; q < n; ++q)
@@ -700,6 +716,17 @@ impir_status impir_get_config(int32_t h, uint32_t n_queries, impir_config* cfg) 
     DeviceState* dev;
     if (impir_status s = need_device(&dev)) return s;
     *cfg = config_for(db, n_queries ? n_queries : 1, dev->sms);
+    return IMPIR_OK;
+}
+
+impir_status impir_get_config_add32(int32_t h, uint32_t n_queries, impir_config* cfg) {
+    if (!cfg) return fail(IMPIR_EINVAL, "NULL argument");
+    Db db;
+    if (impir_status s = get_db(h, &db)) return s;
+    DeviceState* dev;
+    if (impir_status s = need_device(&dev)) return s;
+    const uint32_t n = n_queries ? n_queries : 1;
+    *cfg = add_config(db.cfg_set ? db.cfg : default_add_config(db.n, db.stride / 16, n, dev->sms), db.stride / 16);
     return IMPIR_OK;
 }
 

@@ -120,7 +120,8 @@ cudaError_t launch_fused(uint32_t qpw, uint32_t nk, dim3 grid, dim3 block, size_
 cudaError_t launch_fused_q1(uint32_t nk, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const FusedParams& p);
 cudaError_t launch_fused_q2(uint32_t nk, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const FusedParams& p);
 cudaError_t launch_fused_q4(uint32_t nk, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const FusedParams& p);
-cudaError_t launch_fused_add(uint32_t nk, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const FusedParams& p);
+cudaError_t launch_fused_add(uint32_t qc, uint32_t nk, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             const FusedParams& p);
 cudaError_t launch_fused_q16(uint32_t nk, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const FusedParams& p);
 cudaError_t launch_fused_q8(uint32_t nk, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const FusedParams& p);
 
