@@ -147,8 +147,10 @@ impir_status impir_answer(int32_t db_handle, const uint8_t* keys, uint32_t n_que
  *   out[q] = sum over j < min(N, 2^m) of (-1)^b * low32(Eval(k, j)) * D[j]   (mod 2^32, per word)
  * where low32 is bytes 0..3 of the 128-bit leaf read little-endian. Keys from dpf_gen give
  * r_0 + r_1 = D[alpha]. Same arguments and errors as impir_answer / impir_answer_async, plus
- * EINVAL when record_bytes is not a multiple of 4. Launch shape: one query per warp tile and
- * at most 2^5 leaves per lane (one 32-bit share per leaf is kept in shared memory). */
+ * EINVAL when record_bytes is not a multiple of 4. Launch shape (impir_get_config_add32): the
+ * database's configuration narrowed to 1 or 2 queries per warp tile (2 for records up to
+ * 2 KiB) and at most 16 warps; any lane_bits (the 32-bit shares are kept in shared memory for
+ * 32 / queries leaves per lane at a time and scanned chunk by chunk). */
 impir_status impir_answer_add32(int32_t db_handle, const uint8_t* keys, uint32_t n_queries, uint8_t* out);
 impir_status impir_answer_add32_async(int32_t db_handle, const uint8_t* d_keys, const uint32_t* d_key_offsets,
                                       uint32_t n_queries, uint8_t* d_out, void* d_workspace, size_t workspace_bytes,
