@@ -584,6 +584,31 @@ def main():
         additive = {"queries": len(sub), "add32_queries_per_s": len(sub) / t_add, "xor_queries_per_s": len(sub) / t_xor,
                     "reconstructed_ok": ok, "launch": impir.impir_get_config_add32(dbh, len(sub)).as_dict()}
 
+    # latency of one query through the synchronous call (host key in, answer out) on the
+    # single-query workload: N = 2^16 x 32 B (2 MiB), m = 16, both servers' keys
+    single = None
+    if rank == 0:
+        sw = workloads.single_query()
+        sdb = workloads.make_db(sw.n_records, sw.record_bytes, sw.db_seed)
+        sh = impir.impir_db_load(sdb, sw.n_records, sw.record_bytes)
+        try:
+            b = sw.batches[0]
+            k0, k1 = impir.dpf_gen(b.alphas[0], b.ms[0], 0, b.seeds[0])
+            for _ in range(5):
+                impir.impir_answer(sh, k0, 1, sw.record_bytes)
+            lat = []
+            for i in range(100):
+                t0 = time.perf_counter()
+                r = impir.impir_answer(sh, k0 if i % 2 == 0 else k1, 1, sw.record_bytes)
+                lat.append(time.perf_counter() - t0)
+            r0 = impir.impir_answer(sh, k0, 1, sw.record_bytes)
+            r1 = impir.impir_answer(sh, k1, 1, sw.record_bytes)
+            single = {"workload": sw.name, "median_us": statistics.median(lat) * 1e6,
+                      "p99_us": sorted(lat)[98] * 1e6, "calls": len(lat),
+                      "reconstructed": bool(np.array_equal(r0[0] ^ r1[0], sdb[b.alphas[0]]))}
+        finally:
+            impir.impir_db_free(sh)
+
     # bulk update bandwidth: 256 MiB of new records into the resident DB (synchronous call)
     upd_n = min((256 << 20) // B, N // 2)
     upd_rec = np.random.default_rng(11).integers(0, 256, (upd_n, B), dtype=np.uint8)
@@ -628,6 +653,7 @@ def main():
             "cpu_baseline": cpu,
             "serving": serving,
             "db_update": db_update,
+            "single_query_latency": single,
             "streamed": streamed,
             "additive": additive,
             "setup_s": setup_s,
