@@ -346,6 +346,10 @@ impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_conf
         g_timing.pending.emplace_back(ev0, ev1);
         g_timing.fused += 1;
     }
+    if (!d_out) {  // the caller reads the answers from the accumulators itself
+        count_launches(2);
+        return IMPIR_OK;
+    }
     count_launches(3);
 
     FinalizeParams zp{};
@@ -359,12 +363,15 @@ impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_conf
     return IMPIR_OK;
 }
 
+// direct_out: no finalize kernel; the answers stay in the workspace's accumulators (one
+// launch for the batch only), where the synchronous path downloads them from
 impir_status answer_async_impl(const Db& db, const impir_config* cfg_in, const uint8_t* d_keys, const uint32_t* d_off,
-                               uint32_t n, uint8_t* d_out, void* d_ws, size_t ws_bytes, cudaStream_t st, int mode = 0) {
+                               uint32_t n, uint8_t* d_out, void* d_ws, size_t ws_bytes, cudaStream_t st, int mode = 0,
+                               bool direct_out = false) {
     DeviceState* dev;
     if (impir_status s = need_device(&dev)) return s;
     if (n == 0) return IMPIR_OK;
-    if (!d_keys || !d_off || !d_out || !d_ws) return fail(IMPIR_EINVAL, "NULL device buffer");
+    if (!d_keys || !d_off || (!d_out && !direct_out) || !d_ws) return fail(IMPIR_EINVAL, "NULL device buffer");
     if (reinterpret_cast<uintptr_t>(d_ws) & 255) return fail(IMPIR_EINVAL, "workspace must be 256-byte aligned");
     impir_config cfg = cfg_in                      ? *cfg_in
                        : (mode == 1 && !db.cfg_set) ? default_add_config(db.n, db.stride / 16, n, dev->sms)
@@ -375,6 +382,7 @@ impir_status answer_async_impl(const Db& db, const impir_config* cfg_in, const u
     }
     if (impir_status s = check_config(cfg, db.stride / 16, mode)) return s;
     if (cfg.queries_per_launch == 1) {
+        if (direct_out) return fail(IMPIR_EINVAL, "direct answers need one launch for the batch");
         if (ws_bytes < ws_layout(1, db.stride).total) return fail(IMPIR_ENOMEM, "workspace too small");
         for (uint32_t q = 0; q < n; ++q)
             if (impir_status s = launch_batch(*dev, db, cfg, d_keys, d_off + q, 1, d_out + size_t(q) * db.bytes,
@@ -385,15 +393,16 @@ impir_status answer_async_impl(const Db& db, const impir_config* cfg_in, const u
     if (ws_bytes < ws_layout(n, db.stride).total)
         return fail(IMPIR_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed", ws_bytes,
                     ws_layout(n, db.stride).total);
-    return launch_batch(*dev, db, cfg, d_keys, d_off, n, d_out, static_cast<uint8_t*>(d_ws), st, mode);
+    return launch_batch(*dev, db, cfg, d_keys, d_off, n, direct_out ? nullptr : d_out, static_cast<uint8_t*>(d_ws), st,
+                        mode);
 }
 
 // ---- synchronous path context: cached device and pinned buffers ----
 struct SyncCtx {
     std::mutex mu;
     cudaStream_t stream = nullptr;
-    void *d_keys = nullptr, *d_off = nullptr, *d_ws = nullptr, *d_out = nullptr;
-    size_t c_keys = 0, c_off = 0, c_ws = 0, c_out = 0;
+    void *d_keys = nullptr, *d_ws = nullptr, *d_out = nullptr;  // d_keys: keys, then their offsets
+    size_t c_keys = 0, c_ws = 0, c_out = 0;
     uint8_t* h_stage = nullptr;
     size_t c_stage = 0;
 };
@@ -671,24 +680,29 @@ static impir_status answer_sync(int32_t h, const uint8_t* keys, uint32_t n, uint
     std::lock_guard<std::mutex> lk(g_sync.mu);
     if (!g_sync.stream) CK(cudaStreamCreateWithFlags(&g_sync.stream, cudaStreamNonBlocking), "stream create");
     const impir_config cfg = config_for(db, n, dev->sms);
-    const size_t ws = cfg.queries_per_launch == 1 ? ws_layout(1, db.stride).total : ws_layout(n, db.stride).total;
+    // records without padding and one launch for the batch: the answers are downloaded straight
+    // from the accumulators (no finalize kernel); keys and their offsets go up in one copy
+    const bool direct = cfg.queries_per_launch == 0 && db.stride == db.bytes;
+    const WsLayout lay = ws_layout(cfg.queries_per_launch == 1 ? 1 : n, db.stride);
     const size_t out_bytes = size_t(n) * db.bytes;
-    const size_t stage = std::max(total + size_t(n) * 4, out_bytes);
-    if (impir_status s = grow(&g_sync.d_keys, &g_sync.c_keys, total)) return s;
-    if (impir_status s = grow(&g_sync.d_off, &g_sync.c_off, size_t(n) * 4)) return s;
-    if (impir_status s = grow(&g_sync.d_ws, &g_sync.c_ws, ws)) return s;
-    if (impir_status s = grow(&g_sync.d_out, &g_sync.c_out, out_bytes)) return s;
+    const size_t koff = (total + 15) & ~size_t(15), up = koff + size_t(n) * 4;
+    const size_t stage = std::max(up, out_bytes);
+    if (impir_status s = grow(&g_sync.d_keys, &g_sync.c_keys, up)) return s;
+    if (impir_status s = grow(&g_sync.d_ws, &g_sync.c_ws, lay.total)) return s;
+    if (!direct)
+        if (impir_status s = grow(&g_sync.d_out, &g_sync.c_out, out_bytes)) return s;
     if (impir_status s = grow(reinterpret_cast<void**>(&g_sync.h_stage), &g_sync.c_stage, stage, true)) return s;
     std::memcpy(g_sync.h_stage, keys, total);
-    std::memcpy(g_sync.h_stage + total, offs.data(), size_t(n) * 4);
+    std::memcpy(g_sync.h_stage + koff, offs.data(), size_t(n) * 4);
     cudaStream_t st = g_sync.stream;
-    CK(cudaMemcpyAsync(g_sync.d_keys, g_sync.h_stage, total, cudaMemcpyHostToDevice, st), "key upload");
-    CK(cudaMemcpyAsync(g_sync.d_off, g_sync.h_stage + total, size_t(n) * 4, cudaMemcpyHostToDevice, st), "offset upload");
-    if (impir_status s = answer_async_impl(db, &cfg, static_cast<const uint8_t*>(g_sync.d_keys),
-                                           static_cast<const uint32_t*>(g_sync.d_off), n,
-                                           static_cast<uint8_t*>(g_sync.d_out), g_sync.d_ws, g_sync.c_ws, st, mode))
+    uint8_t* d_keys = static_cast<uint8_t*>(g_sync.d_keys);
+    CK(cudaMemcpyAsync(d_keys, g_sync.h_stage, up, cudaMemcpyHostToDevice, st), "key upload");
+    if (impir_status s = answer_async_impl(db, &cfg, d_keys, reinterpret_cast<const uint32_t*>(d_keys + koff), n,
+                                           static_cast<uint8_t*>(g_sync.d_out), g_sync.d_ws, g_sync.c_ws, st, mode,
+                                           direct))
         return s;
-    CK(cudaMemcpyAsync(g_sync.h_stage, g_sync.d_out, out_bytes, cudaMemcpyDeviceToHost, st), "answer download");
+    const void* src = direct ? static_cast<const void*>(static_cast<uint8_t*>(g_sync.d_ws) + lay.off_acc) : g_sync.d_out;
+    CK(cudaMemcpyAsync(g_sync.h_stage, src, out_bytes, cudaMemcpyDeviceToHost, st), "answer download");
     CK(cudaStreamSynchronize(st), "answer");
     std::memcpy(out, g_sync.h_stage, out_bytes);
     return IMPIR_OK;
