@@ -531,17 +531,23 @@ def main():
         # a pinned (page-locked) host copy of the DB: copies then run at link speed
         pinned = torch.empty(N * B, dtype=torch.uint8, pin_memory=True)
         pinned.copy_(torch.from_numpy(db.reshape(-1)))
-        t0 = time.perf_counter()
-        res = impir.impir_answer(dbh, big["blob0"], big["n"], B)
-        t_res = time.perf_counter() - t0
+        tr = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            res = impir.impir_answer(dbh, big["blob0"], big["n"], B)
+            tr.append(time.perf_counter() - t0)
+        t_res = statistics.median(tr)
         # the first call allocates the staging buffers (kept for later calls); the second is
         # the steady state of repeated calls
         t0 = time.perf_counter()
         got, scfg = impir.impir_answer_streamed(pinned.data_ptr(), N, B, big["blob0"], big["n"], 1 << 30)
         t_first = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        got2, _ = impir.impir_answer_streamed(pinned.data_ptr(), N, B, big["blob0"], big["n"], 1 << 30)
-        t_str = time.perf_counter() - t0
+        warm = []
+        for _ in range(3):  # call-to-call spread is a few per cent: report the median
+            t0 = time.perf_counter()
+            got2, _ = impir.impir_answer_streamed(pinned.data_ptr(), N, B, big["blob0"], big["n"], 1 << 30)
+            warm.append(time.perf_counter() - t0)
+        t_str = statistics.median(warm)
         dev_buf = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
         dev_buf.copy_(pinned[: 1 << 30], non_blocking=True)
         torch.cuda.synchronize()
@@ -554,6 +560,7 @@ def main():
         streamed = {"queries": big["n"], "db_bytes": N * B, "chunk_bytes": 1 << 30, "host_memory": "pinned",
                     "resident_queries_per_s": big["n"] / t_res, "streamed_queries_per_s": big["n"] / t_str,
                     "streamed_over_resident": t_res / t_str, "first_call_queries_per_s": big["n"] / t_first,
+                    "warm_calls_queries_per_s": [big["n"] / t for t in warm],
                     "h2d_link_gb_per_s": link, "db_stream_gb_per_s": N * B / t_str / 1e9,
                     "bit_identical": bool(np.array_equal(got, res) and np.array_equal(got2, res)),
                     "launch": scfg}

@@ -149,8 +149,9 @@ impir_status impir_answer(int32_t db_handle, const uint8_t* keys, uint32_t n_que
  * r_0 + r_1 = D[alpha]. Same arguments and errors as impir_answer / impir_answer_async, plus
  * EINVAL when record_bytes is not a multiple of 4. Launch shape (impir_get_config_add32): the
  * database's configuration narrowed to 1 or 2 queries per warp tile (2 for records up to
- * 2 KiB) and at most 16 warps; any lane_bits (the 32-bit shares are kept in shared memory for
- * 32 / queries leaves per lane at a time and scanned chunk by chunk). */
+ * 2 KiB) and, for records above 512 bytes, at most 16 warps; any lane_bits (the 32-bit shares
+ * are kept in shared memory for 32 / queries leaves per lane at a time and scanned chunk by
+ * chunk). */
 impir_status impir_answer_add32(int32_t db_handle, const uint8_t* keys, uint32_t n_queries, uint8_t* out);
 impir_status impir_answer_add32_async(int32_t db_handle, const uint8_t* d_keys, const uint32_t* d_key_offsets,
                                       uint32_t n_queries, uint8_t* d_out, void* d_workspace, size_t workspace_bytes,
@@ -188,8 +189,8 @@ impir_status impir_workspace_status(const void* d_workspace, uint32_t* n_bad, ui
  *   queries_per_warp   queries evaluated per warp tile before one shared scan of the
  *                      tile (1, 2, 4, 8, or 16 for records of at most 512 bytes): the DB
  *                      tile is read once for all of them
- *   warps_per_cta      4..16; up to 20 for the XOR answer with records of at most 512 bytes
- *                      and at most 8 queries per warp (the additive answer uses at most 16)
+ *   warps_per_cta      4..16; up to 20 for records of at most 512 bytes and at most 8
+ *                      queries per warp
  *   queries_per_launch 0 = the whole batch in one persistent launch; 1 = the plain
  *                      one-query-per-launch form (one launch per key, in order) */
 typedef struct {
@@ -207,7 +208,8 @@ impir_status impir_set_config(int32_t db_handle, const impir_config* cfg);
 
 /* The launch shape impir_answer_add32[_async] would use for a batch of n_queries keys on this
  * database: the configuration set or tuned for it narrowed to the additive kernels (1 or 2
- * queries per warp tile, at most 16 warps), else the additive default. */
+ * queries per warp tile; at most 16 warps for records above 512 bytes), else the additive
+ * default. */
 impir_status impir_get_config_add32(int32_t db_handle, uint32_t n_queries, impir_config* cfg);
 
 /* Times candidate configurations on the given asynchronous problem (same arguments as

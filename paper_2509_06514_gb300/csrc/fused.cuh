@@ -729,9 +729,9 @@ __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_ba
 
 
 template <int QC, int NK, int MODE = 0>
-// Up to 640 threads (20 warps) for the XOR answer with one column pass and at most 8 queries
-// per warp, which fit in 102 registers; 512 for the others, which need more.
-__global__ void __launch_bounds__((MODE == 0 && NK == 1 && QC <= 8) ? 640 : 512, 1)
+// Up to 640 threads (20 warps) for one column pass (records of at most 512 bytes) and at most
+// 8 queries per warp, which fit in 102 registers; 512 for the others, which need more.
+__global__ void __launch_bounds__((NK == 1 && QC <= 8) ? 640 : 512, 1)
     fused_kernel(const __grid_constant__ FusedParams P) {
     static_assert(MODE == 0 || QC * NK <= 8, "additive accumulators: at most 8 uint4 per lane");
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;

@@ -259,7 +259,7 @@ uint32_t add_share_words(const impir_config& c) {
 
 impir_config add_config(impir_config c, uint32_t words) {
     c.queries_per_warp = std::min(c.queries_per_warp, max_add_qpw(words));
-    if (c.warps_per_cta > 16) c.warps_per_cta = 16;  // the additive kernels are built for 16 warps
+    if (c.warps_per_cta > 16 && nk_for(words) > 1) c.warps_per_cta = 16;  // wider records: 16-warp kernels
     return c;
 }
 

@@ -74,18 +74,21 @@ def test_additive_chunked_lane_subtrees(built, orc, qpw, lane_bits, N, B):
         impir.impir_db_free(h)
 
 
-def test_additive_on_a_database_set_to_20_warps(built, orc):
-    """A launch shape of 20 warps and 8 queries per warp (XOR answer) is narrowed to 16 warps and
-    2 queries per warp tile for the additive one, which impir_get_config_add32 reports."""
-    N, B = 30000, 256
-    db = workloads.make_db(N, B, seed=2020)
+@pytest.mark.parametrize("B,shape,want", [(256, (7, 8, 20), (7, 2, 20)), (1024, (6, 8, 16), (6, 2, 16)),
+                                          (4100, (6, 2, 16), (6, 1, 16))])
+def test_additive_shape_from_the_database_configuration(built, orc, B, shape, want):
+    """The XOR answer's configuration (e.g. 20 warps, 8 queries per warp) is narrowed for the
+    additive kernels (2 queries per warp tile, 1 above 2 KiB records; 16 warps above 512 B),
+    which impir_get_config_add32 reports, and the answers stay exact."""
+    N = 30000 if B <= 1024 else 3000
+    db = workloads.make_db(N, B, seed=2020 + B)
     rng = np.random.default_rng(2020)
-    keys = [random_key(rng, m, 0, i % 2) for i, m in enumerate([15, 15, 13])]
+    keys = [random_key(rng, m, 0, i % 2) for i, m in enumerate([15, 15, 12] if B <= 1024 else [12, 12, 11])]
     h = impir.impir_db_load(db, N, B)
     try:
-        impir.impir_set_config(h, 7, 8, 20, 0)
+        impir.impir_set_config(h, *shape, 0)
         c = impir.impir_get_config_add32(h, len(keys)).as_dict()
-        assert (c["lane_bits"], c["queries_per_warp"], c["warps_per_cta"]) == (7, 2, 16)
+        assert (c["lane_bits"], c["queries_per_warp"], c["warps_per_cta"]) == want
         got = impir.impir_answer_add32(h, b"".join(keys), len(keys), B)
         for i, k in enumerate(keys):
             assert got[i].tobytes() == orc.answer_add32(k, db, N, B), i
