@@ -588,8 +588,12 @@ def main():
         s32 = (a0.view("<u4").astype(np.uint64) + a1.view("<u4").astype(np.uint64)) % (1 << 32)
         rec = s32.astype("<u4").view(np.uint8).reshape(len(sub), B)
         ok = sum(int(np.array_equal(rec[i], db[a])) for i, a in enumerate(al))
+        add_blocks = sum(aes_blocks(bt["ms"][i]) for bt, i in sub)
         additive = {"queries": len(sub), "add32_queries_per_s": len(sub) / t_add, "xor_queries_per_s": len(sub) / t_xor,
-                    "reconstructed_ok": ok, "launch": impir.impir_get_config_add32(dbh, len(sub)).as_dict()}
+                    "reconstructed_ok": ok, "launch": impir.impir_get_config_add32(dbh, len(sub)).as_dict(),
+                    # same AES work as the XOR answer (one block per tree edge), wall time of one call
+                    "aes_gaes_per_s": add_blocks / t_add / 1e9,
+                    "frac_of_peak": (add_blocks / t_add / 1e9 / peak) if peak else None}
 
     # latency of one query through the synchronous call (host key in, answer out) on the
     # single-query workload: N = 2^16 x 32 B (2 MiB), m = 16, both servers' keys
