@@ -243,8 +243,6 @@ void count_launches(uint64_t n) {
 }
 
 // ---- launches ----
-// Launch shape of the additive answer derived from a configuration: one query per warp tile
-// and a lane subtree small enough for one 32-bit share per leaf in shared memory.
 // The additive answer takes 1 or 2 queries per warp tile (records up to 2 KiB: 2, else 1; with
 // 4 the extra walk states and smaller chunks cost more than the shared record loads save), and
 // keeps one 32-bit share per leaf for 32 / queries leaves per lane at a time and query (larger
