@@ -49,6 +49,7 @@ def parse_args():
     p.add_argument("--cpu-sample", type=int, default=2, help="queries in the oracle's timed sample")
     p.add_argument("--no-serving", action="store_true", help="skip the serving sweep (three resident DBs)")
     p.add_argument("--no-streamed", action="store_true", help="skip the host-streamed database measurement")
+    p.add_argument("--no-shards", action="store_true", help="skip the row-shard measurement")
     p.add_argument("--serving-requests", type=int, default=2000, help="requests per arrival rate")
     return p.parse_args()
 
@@ -595,6 +596,50 @@ def main():
                     "aes_gaes_per_s": add_blocks / t_add / 1e9,
                     "frac_of_peak": (add_blocks / t_add / 1e9 / peak) if peak else None}
 
+    # row shards (the multi-GPU split of one database, timed here on one GPU): the largest batch
+    # answered on two row-shard handles of the DB, partial answers combined on the device, against
+    # the whole DB; with one shard per GPU the step would take the slower shard plus the exchange
+    row_shards = None
+    if rank == 0 and not args.no_shards:
+        from paper_2509_06514_gb300.sharding import combine, domain_weights, shard_rows
+        big = max(batches, key=lambda bt: bt["n"])
+        # split at half the batch's work (its domains cover DB prefixes), not half the rows
+        blocks = shard_rows(N, 2, weights=domain_weights(N, big["ms"]))
+        hs = [impir.impir_db_load_rows(db[lo:lo + n], n, B, lo, N) for lo, n in blocks]
+        try:
+            for hh in hs:
+                impir.impir_set_config(hh, **{k: cfg[k] for k in ("lane_bits", "queries_per_warp", "warps_per_cta")})
+            nq, d_keys, d_off, d_ws, wsb = big["n"], big["d_keys0"], big["d_off"], big["d_ws"], big["wsb"]
+            parts = torch.zeros((2, nq, B), dtype=torch.uint8, device="cuda")
+            whole = torch.zeros((nq, B), dtype=torch.uint8, device="cuda")
+            st = torch.cuda.Stream()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            times = {"whole": [], "shard0": [], "shard1": [], "combine": []}
+            with torch.cuda.stream(st):
+                for rep in range(3):
+                    ev[0].record(st)
+                    impir.impir_answer_async(dbh, d_keys, d_off, nq, whole, d_ws, wsb, st)
+                    ev[1].record(st)
+                    impir.impir_answer_async(hs[0], d_keys, d_off, nq, parts[0], d_ws, wsb, st)
+                    ev[2].record(st)
+                    impir.impir_answer_async(hs[1], d_keys, d_off, nq, parts[1], d_ws, wsb, st)
+                    ev[3].record(st)
+                    out = combine(parts, 0, st)
+                    ev[4].record(st)
+                    st.synchronize()
+                    for name, a, b in (("whole", 0, 1), ("shard0", 1, 2), ("shard1", 2, 3), ("combine", 3, 4)):
+                        times[name].append(ev[a].elapsed_time(ev[b]))
+            med = {k: statistics.median(v) for k, v in times.items()}
+            row_shards = {"queries": nq, "shards": [{"row_lo": lo, "rows": n} for lo, n in blocks],
+                          "ms": med, "bit_identical": bool(torch.equal(out, whole)),
+                          "shards_sum_over_whole": (med["shard0"] + med["shard1"]) / med["whole"],
+                          "two_gpu_projection_queries_per_s": nq / ((max(med["shard0"], med["shard1"]) + med["combine"]) / 1e3),
+                          "note": "one GPU; the projection leaves out the all-gather of 2 x Q x B bytes"}
+            del parts, whole
+        finally:
+            for hh in hs:
+                impir.impir_db_free(hh)
+
     # latency of one query through the synchronous call (host key in, answer out) on the
     # single-query workload: N = 2^16 x 32 B (2 MiB), m = 16, both servers' keys
     single = None
@@ -665,6 +710,7 @@ def main():
             "serving": serving,
             "db_update": db_update,
             "single_query_latency": single,
+            "row_shards": row_shards,
             "streamed": streamed,
             "additive": additive,
             "setup_s": setup_s,

@@ -38,6 +38,35 @@ def test_shard_rows_cover_the_database_in_aligned_blocks(n_total, world):
         assert max(sizes) - min(sizes) <= 2 * IMPIR_SHARD_ALIGN
 
 
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("world", [2, 3, 5])
+def test_weighted_shard_rows_balance_the_work(seed, world):
+    from paper_2509_06514_gb300.sharding import domain_weights
+    rng = np.random.default_rng(seed)
+    n_total = int(rng.integers(1, 40)) * IMPIR_SHARD_ALIGN + int(rng.integers(0, IMPIR_SHARD_ALIGN))
+    units = -(-n_total // IMPIR_SHARD_ALIGN)
+    weights = rng.integers(0, 10, units).tolist() if seed % 2 else \
+        domain_weights(n_total, rng.integers(15, 27, 50).tolist())
+    blocks = shard_rows(n_total, world, weights=weights)
+    pos, work = 0, []
+    for lo, n in blocks:
+        assert lo == pos and (lo % IMPIR_SHARD_ALIGN == 0 or n == 0)
+        assert lo + n == n_total or (lo + n) % IMPIR_SHARD_ALIGN == 0
+        work.append(sum(weights[lo // IMPIR_SHARD_ALIGN:-(-(lo + n) // IMPIR_SHARD_ALIGN)]) if n else 0)
+        pos = lo + n
+    assert pos == n_total
+    # every shard's work is at most its share plus one block's
+    assert max(work) <= sum(weights) / world + max(weights) + 1e-9
+    with pytest.raises(ValueError):
+        shard_rows(n_total, world, weights=weights[:-1] if len(weights) > 1 else [-1])
+
+
+def test_domain_weights_count_covering_queries():
+    from paper_2509_06514_gb300.sharding import domain_weights
+    a = IMPIR_SHARD_ALIGN
+    assert domain_weights(4 * a, [15, 16, 17, 40]) == [4, 3, 2, 2]   # 2^15 = a, 2^16 = 2a, 2^17 = 4a
+
+
 def test_shard_rows_rejects_empty():
     with pytest.raises(ValueError):
         shard_rows(0, 2)
