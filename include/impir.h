@@ -225,7 +225,7 @@ impir_status impir_autotune(int32_t db_handle, const uint8_t* d_keys, const uint
 /* Database larger than device memory (§3.3: evaluate the linear operations over the DB in
  * batches of chunks): answers n_queries host keys against n_records records of record_bytes
  * each that stay in host memory `records`, streaming them through the device in chunks of
- * about chunk_bytes (rounded to whole warp tiles; the first chunk a quarter of that), two
+ * about chunk_bytes (0: 2 GiB; rounded to whole warp tiles; the first chunk a quarter of that), two
  * chunk buffers deep, the copy of one chunk overlapping the fused launches on earlier ones.
  * Consecutive chunks alternate between two compute streams with their own work schedules, so
  * one chunk's launch starts on the SMs the previous one frees; per-query accumulators are

@@ -829,6 +829,7 @@ impir_status impir_answer_streamed(const void* records, uint64_t N, uint32_t B, 
     const impir_config cfg = default_config(N, words, n, dev->sms);
     if (used) *used = cfg;
     const uint64_t T = 32ull << cfg.lane_bits;  // warp tile: chunks hold whole tiles
+    if (chunk_bytes == 0) chunk_bytes = 2ull << 30;  // default: 2 GiB (fewer launch tails, small first copy)
     uint64_t chunk = (chunk_bytes / stride) / T * T;
     if (chunk < T) chunk = T;
     if (chunk > N) chunk = (N + T - 1) / T * T;

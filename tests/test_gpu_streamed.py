@@ -28,6 +28,7 @@ def keys_for(rng, N, ms, prf=0):
     (300001, 40, 5 << 20, [19, 19, 17, 12, 19]),
     (70000, 1024, 1, [17, 16, 10]),          # chunk rounded up to one warp tile
     (5000, 64, 1 << 30, [13, 12, 5]),        # chunk larger than the DB
+    (1 << 20, 64, 0, [20, 19, 11]),          # the default chunk size
 ])
 def test_streamed_equals_resident(built, orc, N, B, chunk_bytes, ms):
     rng = np.random.default_rng(N + B)
