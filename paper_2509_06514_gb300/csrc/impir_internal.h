@@ -79,9 +79,10 @@ struct SetupParams {
     uint32_t words;          // stride / 16
     uint32_t lane_bits;
     uint32_t qpw;            // queries per warp (group size)
-    // Streaming a database in chunks: only warp tiles in [tile_lo, tile_hi) are scheduled
-    // (tile_hi == 0: no upper limit), and keep_acc != 0 keeps the accumulators of the
-    // previous chunks instead of zeroing them. Zero values give the whole-database launch.
+    // A chunk of a streamed database or a row shard: only warp tiles in [tile_lo, tile_hi)
+    // are scheduled (tile_hi == 0: no upper limit), and keep_acc != 0 keeps the accumulators
+    // of the previous chunks instead of zeroing them. Zero values give the whole-database
+    // launch.
     unsigned long long tile_lo, tile_hi;
     uint32_t keep_acc;
 };
@@ -97,9 +98,9 @@ struct FusedParams {
     uint32_t n_queries;
     uint32_t words;          // uint4 words per record (stride / 16)
     uint32_t lane_bits;
-    uint32_t bits_words;     // 32-bit words of selection bits per (warp, query slot)
+    uint32_t bits_words;     // 32-bit words of selection bits (additive: shares) per (warp, query slot)
     uint32_t mmo_rk[2][44];  // round keys of the fixed MMO keys K_0, K_1
-    unsigned long long rec_lo;  // global index of the record at db[0] (0 unless streaming)
+    unsigned long long rec_lo;  // global index of the record at db[0] (0 unless a chunk or a row shard)
 };
 
 struct FinalizeParams {
