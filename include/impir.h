@@ -188,7 +188,8 @@ impir_status impir_workspace_status(const void* d_workspace, uint32_t* n_bad, ui
  *                      (a warp tile is 32 * 2^lane_bits records); 0..10
  *   queries_per_warp   queries evaluated per warp tile before one shared scan of the
  *                      tile (1, 2, 4, 8, or 16 for records of at most 512 bytes): the DB
- *                      tile is read once for all of them
+ *                      tile is read once for all of them (records above 512 bytes in column
+ *                      passes of up to 16 / queries_per_warp 16-byte words per lane)
  *   warps_per_cta      4..16; up to 20 for records of at most 512 bytes and at most 8
  *                      queries per warp
  *   queries_per_launch 0 = the whole batch in one persistent launch; 1 = the plain

@@ -124,15 +124,25 @@ int32_t add_db(const Db& d) {
 }
 
 // ---- configuration ----
-uint32_t nk_for(uint32_t words) {
+// uint4 words per lane and pass that cover a record in one pass (1, 2, 4 or 8)
+uint32_t nk_need(uint32_t words) {
     if (words <= 32) return 1;
     const uint32_t need = (words + 31) / 32;
     return need <= 2 ? 2 : need <= 4 ? 4 : 8;
 }
 
+// uint4 words per lane and pass of the XOR scan for qpw queries per warp: records above 512 B
+// are scanned in column passes of nk words per lane, with qpw * nk <= 16 accumulators per lane,
+// so that more queries share every tile read (records of 1 KiB: one pass at 8 queries per warp;
+// 4 KiB: four)
+uint32_t nk_xor(uint32_t words, uint32_t qpw) {
+    if (words <= 32) return 1;
+    return std::min(nk_need(words), std::max(2u, 16u / qpw));
+}
+
 // Widest CTA the fused kernel is built for (its launch bounds): 20 warps for the XOR answer
 // with one column pass (records of at most 512 bytes) and at most 8 queries per warp, else 16.
-uint32_t max_warps(uint32_t qpw, uint32_t words) { return nk_for(words) == 1 && qpw <= 8 ? 20u : 16u; }
+uint32_t max_warps(uint32_t qpw, uint32_t words) { return nk_need(words) == 1 && qpw <= 8 ? 20u : 16u; }
 
 size_t smem_for(const impir_config& c) {
     return kTableBytes + kSegSmemBytes + size_t(c.warps_per_cta) * c.queries_per_warp * (size_t(1) << c.lane_bits) * 4;
@@ -148,7 +158,7 @@ impir_status check_config(const impir_config& c, uint32_t words, int mode = 0) {
     if (c.queries_per_warp != 1 && c.queries_per_warp != 2 && c.queries_per_warp != 4 && c.queries_per_warp != 8 &&
         c.queries_per_warp != 16)
         return fail(IMPIR_EINVAL, "queries_per_warp must be 1, 2, 4, 8 or 16");
-    if (c.queries_per_warp * nk_for(words) > 16)
+    if (c.queries_per_warp * (mode == 0 ? nk_xor(words, c.queries_per_warp) : nk_need(words)) > 16)
         return fail(IMPIR_EINVAL, "queries_per_warp %u too large for %u-byte records", c.queries_per_warp, words * 16);
     if (c.warps_per_cta < 4 || c.warps_per_cta > max_warps(c.queries_per_warp, words))
         return fail(IMPIR_EINVAL, "warps_per_cta must be 4..%u for this record size and queries_per_warp",
@@ -165,7 +175,7 @@ impir_config default_config_warps(uint64_t n_records, uint32_t words, uint32_t n
     c.warps_per_cta = warps;
     c.queries_per_launch = 0;
     uint32_t qpw = 8;
-    while (qpw > 1 && (qpw * nk_for(words) > 16 || qpw > n_queries)) qpw >>= 1;
+    while (qpw > 1 && (qpw * nk_xor(words, qpw) > 16 || qpw > n_queries)) qpw >>= 1;
     c.queries_per_warp = qpw;
     const double all_warps = double(sms) * c.warps_per_cta;
     const double groups = std::ceil(double(n_queries) / qpw);
@@ -247,7 +257,7 @@ void count_launches(uint64_t n) {
 // 4 the extra walk states and smaller chunks cost more than the shared record loads save), and
 // keeps one 32-bit share per leaf for 32 / queries leaves per lane at a time and query (larger
 // lane subtrees are scanned in chunks): 4 KiB per warp.
-uint32_t max_add_qpw(uint32_t words) { return nk_for(words) <= 4 ? 2u : 1u; }
+uint32_t max_add_qpw(uint32_t words) { return nk_need(words) <= 4 ? 2u : 1u; }
 
 // 32-bit share words per query slot of a warp.
 uint32_t add_share_words(const impir_config& c) {
@@ -257,7 +267,7 @@ uint32_t add_share_words(const impir_config& c) {
 
 impir_config add_config(impir_config c, uint32_t words) {
     c.queries_per_warp = std::min(c.queries_per_warp, max_add_qpw(words));
-    if (c.warps_per_cta > 16 && nk_for(words) > 1) c.warps_per_cta = 16;  // wider records: 16-warp kernels
+    if (c.warps_per_cta > 16 && nk_need(words) > 1) c.warps_per_cta = 16;  // wider records: 16-warp kernels
     return c;
 }
 
@@ -332,10 +342,11 @@ impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_conf
         CK(cudaEventRecord(ev0, st), "event record");
     }
     if (mode == 0)
-        CK(launch_fused(cfg.queries_per_warp, nk_for(fp.words), dim3(dev.sms), dim3(cfg.warps_per_cta * 32), smem, st, fp),
+        CK(launch_fused(cfg.queries_per_warp, nk_xor(fp.words, cfg.queries_per_warp), dim3(dev.sms),
+                        dim3(cfg.warps_per_cta * 32), smem, st, fp),
            "fused kernel launch");
     else
-        CK(launch_fused_add(cfg.queries_per_warp, nk_for(fp.words), dim3(dev.sms), dim3(cfg.warps_per_cta * 32), smem,
+        CK(launch_fused_add(cfg.queries_per_warp, nk_need(fp.words), dim3(dev.sms), dim3(cfg.warps_per_cta * 32), smem,
                             st, fp),
            "fused kernel launch (additive)");
     if (timed) {
@@ -931,7 +942,8 @@ impir_status impir_answer_streamed(const void* records, uint64_t N, uint32_t B, 
         fp.rec_lo = lo;
         std::memcpy(fp.mmo_rk, dev->mmo_rk, sizeof fp.mmo_rk);
         if (e == cudaSuccess)
-            e = launch_fused(cfg.queries_per_warp, nk_for(words), dim3(dev->sms), dim3(cfg.warps_per_cta * 32),
+            e = launch_fused(cfg.queries_per_warp, nk_xor(words, cfg.queries_per_warp), dim3(dev->sms),
+                             dim3(cfg.warps_per_cta * 32),
                              smem_for(cfg), ks[b], fp);
         if (e == cudaSuccess) e = cudaEventRecord(consumed[b], ks[b]);
         count_launches(2);

@@ -221,3 +221,24 @@ def test_large_batch_reconstructs(built, orc):
             assert r0[i].tobytes() == orc.answer(pairs[i][0], db, N, B), i
     finally:
         impir.impir_db_free(dbh)
+
+
+@pytest.mark.parametrize("B", [1040, 2064, 4100])
+@pytest.mark.parametrize("cfg", [dict(lane_bits=4, queries_per_warp=8), dict(lane_bits=3, queries_per_warp=4),
+                                 dict(lane_bits=5, queries_per_warp=2)])
+def test_wide_records_in_column_passes(built, orc, B, cfg):
+    """Records above 512 bytes with up to 8 queries per warp: the scan covers each record in
+    several column passes of 16 / queries_per_warp words per lane (ragged last pass)."""
+    N = 3000
+    db = workloads.make_db(N, B, seed=B + cfg["queries_per_warp"])
+    rng = np.random.default_rng(B)
+    ms = [12, 12, 12, 11, 12, 12, 12, 12, 12, 10]
+    keys = [random_key(rng, m, int(i % 2)) for i, m in enumerate(ms)]
+    dbh = impir.impir_db_load(db, N, B)
+    try:
+        impir.impir_set_config(dbh, **cfg)
+        got = gpu_answers(dbh, keys, B)
+        for i, k in enumerate(keys):
+            assert got[i].tobytes() == orc.answer(k, db, N, B), i
+    finally:
+        impir.impir_db_free(dbh)
