@@ -381,6 +381,7 @@ impir_status answer_async_impl(const Db& db, const impir_config* cfg_in, const u
     if (impir_status s = need_device(&dev)) return s;
     if (n == 0) return IMPIR_OK;
     if (!d_keys || !d_off || (!d_out && !direct_out) || !d_ws) return fail(IMPIR_EINVAL, "NULL device buffer");
+    if (!bytes_ok(n, db.stride)) return fail(IMPIR_EINVAL, "batch too large: %u answers of %u bytes", n, db.stride);
     if (reinterpret_cast<uintptr_t>(d_ws) & 255) return fail(IMPIR_EINVAL, "workspace must be 256-byte aligned");
     impir_config cfg = cfg_in                      ? *cfg_in
                        : (mode == 1 && !db.cfg_set) ? default_add_config(db.n, db.stride / 16, n, dev->sms)
@@ -517,9 +518,12 @@ impir_status impir_db_load(const void* records, uint64_t n_records, uint32_t rec
     if (!records || !db_handle) return fail(IMPIR_EINVAL, "NULL argument");
     if (n_records == 0 || record_bytes == 0) return fail(IMPIR_EINVAL, "empty database");
     if (n_records > (1ull << IMPIR_MAX_DOMAIN_BITS)) return fail(IMPIR_EINVAL, "more than 2^40 records");
+    const uint64_t stride = (uint64_t(record_bytes) + 15u) & ~uint64_t(15);
+    if (stride > 0xfffffff0ull || !bytes_ok(n_records, stride))
+        return fail(IMPIR_EINVAL, "database of %llu records of %u bytes is too large", (unsigned long long)n_records,
+                    record_bytes);
     DeviceState* dev;
     if (impir_status s = need_device(&dev)) return s;
-    const uint32_t stride = (record_bytes + 15u) & ~15u;
     void* d = nullptr;
     cudaError_t e = cudaMalloc(&d, size_t(n_records) * stride);
     if (e != cudaSuccess) {
@@ -543,7 +547,7 @@ impir_status impir_db_load(const void* records, uint64_t n_records, uint32_t rec
     db.n = n_records;
     db.n_total = n_records;
     db.bytes = record_bytes;
-    db.stride = stride;
+    db.stride = uint32_t(stride);
     db.owned = true;
     *db_handle = add_db(db);
     return IMPIR_OK;
@@ -553,6 +557,8 @@ impir_status impir_db_load_rows(const void* records, uint64_t n_rows, uint32_t r
                                 uint64_t n_total, int32_t* db_handle) {
     if (!db_handle) return fail(IMPIR_EINVAL, "NULL argument");
     if (n_total > (1ull << IMPIR_MAX_DOMAIN_BITS)) return fail(IMPIR_EINVAL, "more than 2^40 records");
+    if (!bytes_ok(n_total, (uint64_t(record_bytes) + 15u) & ~uint64_t(15)))
+        return fail(IMPIR_EINVAL, "database too large");
     if (n_rows == 0 || row_lo >= n_total || n_rows > n_total - row_lo)
         return fail(IMPIR_EINVAL, "rows [%llu, +%llu) are not inside a database of %llu records",
                     (unsigned long long)row_lo, (unsigned long long)n_rows, (unsigned long long)n_total);
@@ -582,6 +588,7 @@ impir_status impir_db_attach(const void* d_records, uint64_t n_records, uint32_t
     if (n_records == 0 || record_bytes == 0) return fail(IMPIR_EINVAL, "empty database");
     if (n_records > (1ull << IMPIR_MAX_DOMAIN_BITS)) return fail(IMPIR_EINVAL, "more than 2^40 records");
     if (stride_bytes % 16 || stride_bytes < record_bytes) return fail(IMPIR_EINVAL, "bad stride %u", stride_bytes);
+    if (!bytes_ok(n_records, stride_bytes)) return fail(IMPIR_EINVAL, "database too large");
     if (reinterpret_cast<uintptr_t>(d_records) & 15) return fail(IMPIR_EINVAL, "records must be 16-byte aligned");
     Db db;
     db.d = d_records;
@@ -683,6 +690,7 @@ static impir_status answer_sync(int32_t h, const uint8_t* keys, uint32_t n, uint
     if (!keys || !out) return fail(IMPIR_EINVAL, "NULL argument");
     DeviceState* dev;
     if (impir_status s = need_device(&dev)) return s;
+    if (!bytes_ok(n, db.stride)) return fail(IMPIR_EINVAL, "batch too large: %u answers of %u bytes", n, db.stride);
     std::vector<uint32_t> offs;
     size_t total = 0;
     if (impir_status s = parse_host_keys(keys, n, offs, total)) return s;
@@ -830,6 +838,9 @@ impir_status impir_answer_streamed(const void* records, uint64_t N, uint32_t B, 
                                    uint8_t* out, uint64_t chunk_bytes, impir_config* used) {
     if (!records || !keys || !out) return fail(IMPIR_EINVAL, "NULL argument");
     if (N == 0 || B == 0 || N > (1ull << IMPIR_MAX_DOMAIN_BITS)) return fail(IMPIR_EINVAL, "bad database size");
+    if (B > 0xfffffff0u || !bytes_ok(N, (uint64_t(B) + 15u) & ~uint64_t(15)) ||
+        !bytes_ok(n, (uint64_t(B) + 15u) & ~uint64_t(15)))
+        return fail(IMPIR_EINVAL, "database or batch too large");
     if (n == 0) return IMPIR_OK;
     DeviceState* dev;
     if (impir_status s = need_device(&dev)) return s;

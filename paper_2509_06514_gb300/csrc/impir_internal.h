@@ -13,6 +13,12 @@ constexpr uint32_t kMaxLaneBits = 10;     // 2^10 leaves per lane at most
 constexpr uint32_t kMaxSegments = 48;     // one per distinct domain size (<= 41) + slack
 constexpr uint32_t kTableBytes = 128 * 1024;
 
+// Largest byte count of a database, a workspace or an answer buffer the library accepts
+// (1 PiB): products of record counts and strides are checked against it before any
+// allocation or launch, so they never wrap.
+constexpr uint64_t kMaxBytes = 1ull << 50;
+inline bool bytes_ok(uint64_t count, uint64_t unit) { return unit == 0 || count <= kMaxBytes / unit; }
+
 // Workspace header at the start of the device workspace (256 bytes).
 struct WsHeader {
     unsigned long long counter;   // next work unit to hand out

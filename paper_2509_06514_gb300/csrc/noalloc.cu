@@ -93,6 +93,8 @@ extern "C" impir_status impir_answer_noalloc(const void* d_records, uint64_t n_r
     if (stride_bytes % 16 || stride_bytes < record_bytes || (reinterpret_cast<uintptr_t>(d_records) & 15))
         return set_error(IMPIR_EINVAL, "records need a 16-byte stride >= record_bytes and 16-byte alignment");
     if (n_queries == 0) return IMPIR_OK;
+    if (!bytes_ok(n_records, stride_bytes) || !bytes_ok(n_queries, stride_bytes))
+        return set_error(IMPIR_EINVAL, "database or batch too large");
     const WsLayout lay = ws_layout(n_queries, stride_bytes);
     if (lay.total > IMPIR_NOALLOC_SCRATCH_BYTES)
         return set_error(IMPIR_EINVAL,

@@ -105,3 +105,24 @@ def test_tune_cache_round_trip(L, tmp_path):
     assert "152 33554432 256 416 8 4 16 0" in lines and "152 1048576 256 64 5 8 16 0" in lines
     with pytest.raises(impir.ImpirError):
         impir.impir_tune_cache_load(str(tmp_path / "missing.txt"))
+
+
+def test_oversized_inputs_are_rejected_before_any_device_call(L):
+    """Record counts times strides (and batch sizes times strides) that would exceed 1 PiB are
+    rejected with EINVAL before any allocation, copy or launch, so no size product can wrap."""
+    buf = np.zeros(64, np.uint8)
+    p = ctypes.c_void_p(buf.ctypes.data)
+    aligned = ctypes.c_void_p(256)     # never dereferenced: the call fails first
+    h = ctypes.c_int32(0)
+    calls = [
+        lambda: L.impir_db_load(p, 1 << 40, 0xFFFFFF00, ctypes.byref(h)),
+        lambda: L.impir_db_load(p, 1 << 30, 0xFFFFFFFF, ctypes.byref(h)),
+        lambda: L.impir_db_attach(aligned, 1 << 40, 1 << 20, 1 << 20, ctypes.byref(h)),
+        lambda: L.impir_db_load_rows(p, 1, 0xFFFFFF00, 0, 1 << 40, ctypes.byref(h)),
+        lambda: L.impir_answer_streamed(p, 1 << 40, 1 << 20, p, 1, p, 0, None),
+        lambda: L.impir_answer_streamed(p, 16, 0xFFFFFFF8, p, 1, p, 0, None),
+        lambda: L.impir_answer_noalloc(aligned, 1 << 40, 1 << 20, 1 << 20, p, p, 1, p, None),
+    ]
+    for i, call in enumerate(calls):
+        assert call() == impir.IMPIR_EINVAL, i
+        assert b"too large" in L.impir_last_error(), (i, L.impir_last_error())
