@@ -170,7 +170,10 @@ size_t impir_workspace_bytes(uint32_t n_queries, uint32_t stride_bytes);
  *   cuda_stream    a cudaStream_t (NULL = the legacy default stream)
  * Keys are validated on the device: a malformed key's answer is all zero and the first
  * such query index is recorded; read it with impir_workspace_status after the stream
- * completes. Launch errors return ECUDA. */
+ * completes. The device checks each key's header, column 0 and 8-byte alignment, not the
+ * extent of d_keys (the call has no length for it): the caller guarantees that every offset
+ * starts a whole key, impir_key_bytes(m) bytes for the m in its header, inside d_keys.
+ * Launch errors return ECUDA. */
 impir_status impir_answer_async(int32_t db_handle, const uint8_t* d_keys, const uint32_t* d_key_offsets,
                                 uint32_t n_queries, uint8_t* d_out, void* d_workspace, size_t workspace_bytes,
                                 void* cuda_stream);
