@@ -377,7 +377,7 @@ impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_conf
 impir_status answer_async_impl(const Db& db, const impir_config* cfg_in, const uint8_t* d_keys, const uint32_t* d_off,
                                uint32_t n, uint8_t* d_out, void* d_ws, size_t ws_bytes, cudaStream_t st, int mode = 0,
                                bool direct_out = false) {
-    DeviceState* dev;
+    DeviceState* dev = nullptr;
     if (impir_status s = need_device(&dev)) return s;
     if (n == 0) return IMPIR_OK;
     if (!d_keys || !d_off || (!d_out && !direct_out) || !d_ws) return fail(IMPIR_EINVAL, "NULL device buffer");
@@ -522,7 +522,7 @@ impir_status impir_db_load(const void* records, uint64_t n_records, uint32_t rec
     if (stride > 0xfffffff0ull || !bytes_ok(n_records, stride))
         return fail(IMPIR_EINVAL, "database of %llu records of %u bytes is too large", (unsigned long long)n_records,
                     record_bytes);
-    DeviceState* dev;
+    DeviceState* dev = nullptr;
     if (impir_status s = need_device(&dev)) return s;
     void* d = nullptr;
     cudaError_t e = cudaMalloc(&d, size_t(n_records) * stride);
@@ -654,7 +654,7 @@ impir_status impir_db_update_async(int32_t h, uint64_t first, uint64_t n, const 
 }
 
 impir_status impir_db_update(int32_t h, uint64_t first, uint64_t n, const void* records) {
-    DeviceState* dev;
+    DeviceState* dev = nullptr;
     if (impir_status s = need_device(&dev)) return s;
     CK(cudaDeviceSynchronize(), "wait for answers in flight");
     if (impir_status s = impir_db_update_async(h, first, n, records, nullptr, nullptr)) return s;
@@ -688,7 +688,7 @@ static impir_status answer_sync(int32_t h, const uint8_t* keys, uint32_t n, uint
     if (impir_status s = get_db(h, &db)) return s;
     if (n == 0) return IMPIR_OK;
     if (!keys || !out) return fail(IMPIR_EINVAL, "NULL argument");
-    DeviceState* dev;
+    DeviceState* dev = nullptr;
     if (impir_status s = need_device(&dev)) return s;
     if (!bytes_ok(n, db.stride)) return fail(IMPIR_EINVAL, "batch too large: %u answers of %u bytes", n, db.stride);
     std::vector<uint32_t> offs;
@@ -744,7 +744,7 @@ impir_status impir_get_config(int32_t h, uint32_t n_queries, impir_config* cfg) 
     if (!cfg) return fail(IMPIR_EINVAL, "NULL argument");
     Db db;
     if (impir_status s = get_db(h, &db)) return s;
-    DeviceState* dev;
+    DeviceState* dev = nullptr;
     if (impir_status s = need_device(&dev)) return s;
     *cfg = config_for(db, n_queries ? n_queries : 1, dev->sms);
     return IMPIR_OK;
@@ -754,7 +754,7 @@ impir_status impir_get_config_add32(int32_t h, uint32_t n_queries, impir_config*
     if (!cfg) return fail(IMPIR_EINVAL, "NULL argument");
     Db db;
     if (impir_status s = get_db(h, &db)) return s;
-    DeviceState* dev;
+    DeviceState* dev = nullptr;
     if (impir_status s = need_device(&dev)) return s;
     const uint32_t n = n_queries ? n_queries : 1;
     *cfg = add_config(db.cfg_set ? db.cfg : default_add_config(db.n, db.stride / 16, n, dev->sms), db.stride / 16);
@@ -775,7 +775,7 @@ impir_status impir_autotune(int32_t h, const uint8_t* d_keys, const uint32_t* d_
                             void* d_ws, size_t ws_bytes, void* stream, impir_config* best) {
     Db db;
     if (impir_status s = get_db(h, &db)) return s;
-    DeviceState* dev;
+    DeviceState* dev = nullptr;
     if (impir_status s = need_device(&dev)) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const auto key = std::make_tuple(dev->sms, db.n, db.stride, n);
@@ -842,7 +842,7 @@ impir_status impir_answer_streamed(const void* records, uint64_t N, uint32_t B, 
         !bytes_ok(n, (uint64_t(B) + 15u) & ~uint64_t(15)))
         return fail(IMPIR_EINVAL, "database or batch too large");
     if (n == 0) return IMPIR_OK;
-    DeviceState* dev;
+    DeviceState* dev = nullptr;
     if (impir_status s = need_device(&dev)) return s;
     std::vector<uint32_t> offs;
     size_t total = 0;
