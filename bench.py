@@ -41,6 +41,8 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=WORKLOADS, default="uneven8g")
     p.add_argument("--queries", type=int, default=None, help="query count of the batched256m workload (default 64)")
+    p.add_argument("--record-bytes", type=int, default=None,
+                   help="record size of the batched4g workload (a power of two; N = 4 GiB / record size)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true", help="skip the one-query-per-launch comparison")
     p.add_argument("--no-tune", action="store_true")
@@ -54,10 +56,12 @@ def parse_args():
     return p.parse_args()
 
 
-def make_workload(name, queries=None):
+def make_workload(name, queries=None, record_bytes=None):
     from paper_2509_06514_gb300 import workloads as W
     if name == "batched256m" and queries:
         return W.batched_256mib(n_queries=queries)
+    if name == "batched4g" and record_bytes:
+        return W.batched_4gib(record_bytes=record_bytes)
     return {"uneven8g": W.uneven_8gib, "batched4g": W.batched_4gib, "batched256m": W.batched_256mib,
             "single": W.single_query}[name]()
 
@@ -208,7 +212,7 @@ def run_reference(args, world, rank):
     import oracle
     from paper_2509_06514_gb300 import workloads
     oracle.build()
-    w = make_workload(args.workload, args.queries)
+    w = make_workload(args.workload, args.queries, args.record_bytes)
     cores = os.cpu_count() or 1
     # one query per step, taken round-robin from the workload (records regenerated once)
     db = workloads.make_db(w.n_records, w.record_bytes, w.db_seed)
@@ -347,7 +351,7 @@ def main():
 
     torch.cuda.set_device(local)
     build.build()
-    w = make_workload(args.workload, args.queries)
+    w = make_workload(args.workload, args.queries, args.record_bytes)
     N, B = w.n_records, w.record_bytes
     t_setup = time.perf_counter()
     db = workloads.make_db(N, B, w.db_seed)

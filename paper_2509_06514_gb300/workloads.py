@@ -135,11 +135,17 @@ def batched_256mib(seed: int = 1, n_queries: int = 64) -> Workload:
     return w
 
 
-def batched_4gib(seed: int = 2) -> Workload:
-    """Batched GB-scale: N=2^22 x 1 KiB (4 GiB), 256 queries, domain 22 bits."""
+def batched_4gib(seed: int = 2, record_bytes: int = 1024) -> Workload:
+    """Batched GB-scale: 4 GiB of records of record_bytes (a power of two; default 1 KiB:
+    N=2^22), 256 queries whose domain covers the DB (m = log2 N)."""
+    assert record_bytes > 0 and record_bytes & (record_bytes - 1) == 0
+    n = (4 << 30) // record_bytes
+    m = log2_exact(n)
     rng = np.random.default_rng(seed)
-    w = Workload("batched: N=2^22 x 1 KiB, m=22, Q=256", 1 << 22, 1024, seed)
-    w.batches.append(_batch(rng, 256, [22] * 256, w.n_records, seed + 1000, 0))
+    name = (f"batched: N=2^{m} x {record_bytes // 1024} KiB, m={m}, Q=256" if record_bytes >= 1024
+            else f"batched: N=2^{m} x {record_bytes} B, m={m}, Q=256")
+    w = Workload(name, n, record_bytes, seed)
+    w.batches.append(_batch(rng, 256, [m] * 256, w.n_records, seed + 1000, 0))
     return w
 
 
