@@ -601,6 +601,31 @@ def main():
                     "aes_gaes_per_s": add_blocks / t_add / 1e9,
                     "frac_of_peak": (add_blocks / t_add / 1e9 / peak) if peak else None}
 
+    # the fixed-key PRF variant (Matyas-Meyer-Oseas with two fixed AES keys: no key schedule
+    # per node, but no round shared between the two children) on the largest batch, against the
+    # same batch with the keyed PRF; both answers reconstruct their records
+    mmo = None
+    if rank == 0:
+        big = max(batches, key=lambda bt: bt["n"])
+        wb = next(b for b in w.batches if len(b.ms) == big["n"])
+        pairs = [impir.dpf_gen(a, m, impir.IMPIR_PRF_AES_MMO, sd) for m, a, sd in zip(wb.ms, wb.alphas, wb.seeds)]
+        mblob0, _ = impir.pack_keys([p[0] for p in pairs])
+        mblob1, _ = impir.pack_keys([p[1] for p in pairs])
+        impir.impir_answer(dbh, mblob0, big["n"], B)
+        tm, tk = [], []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            m0 = impir.impir_answer(dbh, mblob0, big["n"], B)
+            tm.append(time.perf_counter() - t0)
+            t0 = time.perf_counter()
+            impir.impir_answer(dbh, big["blob0"], big["n"], B)
+            tk.append(time.perf_counter() - t0)
+        m1 = impir.impir_answer(dbh, mblob1, big["n"], B)
+        mmo = {"queries": big["n"], "mmo_queries_per_s": big["n"] / statistics.median(tm),
+               "keyed_queries_per_s": big["n"] / statistics.median(tk),
+               "mmo_over_keyed": statistics.median(tk) / statistics.median(tm),
+               "reconstructed_ok": int(sum(np.array_equal(m0[i] ^ m1[i], db[a]) for i, a in enumerate(big["alphas"])))}
+
     # row shards (the multi-GPU split of one database, timed here on one GPU): the largest batch
     # answered on two row-shard handles of the DB, partial answers combined on the device, against
     # the whole DB; with one shard per GPU the step would take the slower shard plus the exchange
@@ -716,6 +741,7 @@ def main():
             "db_update": db_update,
             "single_query_latency": single,
             "row_shards": row_shards,
+            "mmo_prf": mmo,
             "streamed": streamed,
             "additive": additive,
             "setup_s": setup_s,
