@@ -32,7 +32,7 @@ def test_fips197_sbox_entries(orc):
 def test_aes_matches_library_on_random_inputs(orc):
     ciphers = pytest.importorskip("cryptography.hazmat.primitives.ciphers")
     rng = np.random.default_rng(197)
-    for _ in range(2000):
+    for _ in range(10000):
         key = rng.integers(0, 256, 16, dtype=np.uint8).tobytes()
         pt = rng.integers(0, 256, 16, dtype=np.uint8).tobytes()
         enc = ciphers.Cipher(ciphers.algorithms.AES(key), ciphers.modes.ECB()).encryptor()
