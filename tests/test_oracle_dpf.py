@@ -66,11 +66,12 @@ def test_closed_form_depth_two_with_library_aes(orc, prf):
 
 @pytest.mark.parametrize("prf", [0, 1])
 def test_dpf_property_brute_force(orc, prf):
-    """Eval(k0, j) ^ Eval(k1, j) = [j == alpha] as 128-bit values, every j."""
+    """Eval(k0, j) ^ Eval(k1, j) = [j == alpha] as 128-bit values, every j: every alpha for
+    domains up to 2^10, 16 random alphas for 2^11 and 2^12."""
     one = bytes([1]) + bytes(15)
     rng = np.random.default_rng(11 + prf)
-    for m in range(1, 11):
-        alphas = range(1 << m) if m <= 4 else rng.integers(0, 1 << m, 3)
+    for m in range(1, 13):
+        alphas = range(1 << m) if m <= 10 else rng.integers(0, 1 << m, 16)
         for a in alphas:
             seed = rng.integers(0, 256, 32, dtype=np.uint8).tobytes()
             k0, k1 = orc.gen(int(a), m, prf, seed)
