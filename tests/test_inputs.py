@@ -26,3 +26,16 @@ def test_workload_shapes():
     assert set(m for b in w.batches for m in b.ms) <= {23, 24, 25}
     for b in w.batches:
         assert all(0 <= a < (1 << m) for a, m in zip(b.alphas, b.ms))
+    # the documented split of the benchmark workload (seeded)
+    assert [len(b.ms) for b in w.batches] == [416, 178, 379, 51]
+
+
+def test_batched_4gib_record_sizes():
+    for b in (32, 256, 1024, 4096):
+        w = workloads.batched_4gib(record_bytes=b)
+        assert w.n_records * w.record_bytes == 4 << 30 and w.n_queries == 256
+        assert set(w.batches[0].ms) == {workloads.log2_exact(w.n_records)}
+    # the default (1 KiB records) workload is the one the GPU configuration test answers
+    d = workloads.batched_4gib()
+    assert (d.n_records, d.record_bytes, d.name) == (1 << 22, 1024, "batched: N=2^22 x 1 KiB, m=22, Q=256")
+    assert d.batches[0].alphas == workloads.batched_4gib(record_bytes=1024).batches[0].alphas
