@@ -48,11 +48,14 @@ def parse_args():
     p.add_argument("--no-tune", action="store_true")
     p.add_argument("--config", default=None,
                    help="fixed launch shape lane_bits,queries_per_warp,warps_per_cta (skips autotuning)")
-    p.add_argument("--cpu-sample", type=int, default=2, help="queries in the oracle's timed sample")
+    p.add_argument("--cpu-sample", type=int, default=6,
+                   help="queries in the oracle's timed sample (the workload's domain sizes in turn)")
     p.add_argument("--no-serving", action="store_true", help="skip the serving sweep (three resident DBs)")
     p.add_argument("--no-streamed", action="store_true", help="skip the host-streamed database measurement")
     p.add_argument("--no-shards", action="store_true", help="skip the row-shard measurement")
     p.add_argument("--serving-requests", type=int, default=2000, help="requests per arrival rate")
+    p.add_argument("--calibrate-only", action="store_true",
+                   help="time the AES engines alone (calibration kernel, both PRFs) and exit")
     return p.parse_args()
 
 
@@ -194,14 +197,39 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# Lookups the T-table formulation needs per AES-128 block of the keyed PRF: 16 per round for
-# 10 rounds plus the key schedule's 4 per round shared by the two children of a node.
-LOOKUPS_PER_BLOCK_KEYED = 160 + 20
+# Shared-memory table lookups the fused kernel's keyed T-table engine executes per tree
+# expansion (two AES blocks, both children of a node): an internal node pair costs 345 (key
+# schedule 40, round 1 of both children 17, rounds 2-9 256, final rounds 32), a pair at the
+# leaf level 288 (key schedule 36, round 1 17, rounds 2-8 224, column 0 of round 9 8, the
+# three S-box lookups the selection bits need 3). A domain of 2^m leaves has 2^(m-1) leaf-level
+# pairs and 2^(m-1) - 1 internal ones: 158.25 lookups per AES block on average.
+LOOKUPS_INTERNAL_PAIR = 345
+LOOKUPS_LEAF_PAIR = 288
+# the additive answer's leaf-level pair: the low 32 bits of both leaves (key schedule 36, round 1
+# 17, rounds 2-9 256, column 0 of round 10 and its round-key word 12)
+LOOKUPS_LEAF_PAIR_ADD = 321
 SMEM_LOOKUPS_PER_CLK_PER_SM = 32   # one 32-bit word per bank per clock, 32 banks
 
 
-def aes_peak_gaes(sms: int, mhz: float) -> float:
-    return sms * mhz * 1e6 * SMEM_LOOKUPS_PER_CLK_PER_SM / LOOKUPS_PER_BLOCK_KEYED / 1e9
+def lookups_per_query(m: int, leaf_pair: int = LOOKUPS_LEAF_PAIR) -> int:
+    half = 1 << (m - 1)
+    return leaf_pair * half + LOOKUPS_INTERNAL_PAIR * (half - 1)
+
+
+def smem_peak_gaes(sms: int, mhz: float, lookups_per_block: float) -> float:
+    """AES blocks per second the shared-memory port allows at the kernel's lookups per block."""
+    return sms * mhz * 1e6 * SMEM_LOOKUPS_PER_CLK_PER_SM / lookups_per_block / 1e9
+
+
+def alu_counts():
+    """ALU-pipe instruction counts measured by ncu (committed summary, see profiles/): thread
+    instructions per AES block of the isolated keyed engine and the ALU pipe's peak lanes per
+    SM per clock; None when the summary is absent."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "alu_pipe_counts.json")) as f:
+            return json.load(f)
+    except OSError:
+        return None
 
 
 # ---------------------------------------------------------------- reference arm: the CPU oracle
@@ -336,6 +364,21 @@ def run_serving(args, impir, workloads):
             "points": points}
 
 
+# ---------------------------------------------------------------- AES engine calibration
+
+def calibrate_engines(impir, iters: int = 2000):
+    """The fused kernel's AES engine alone (no tree walk, no scan): every thread of one CTA of
+    512 per SM iterates a node expansion (two AES blocks) in registers; both PRFs."""
+    sms = impir.impir_device_sm_count()
+    n = sms * 512
+    seeds = np.random.default_rng(7).integers(0, 256, (n, 16), dtype=np.uint8)
+    out = {}
+    for prf, name in ((impir.IMPIR_PRF_AES_KEYED, "keyed"), (impir.IMPIR_PRF_AES_MMO, "mmo")):
+        _, ms = impir.impir_aes_calibrate(prf, iters, seeds, 512)
+        out[name] = {"gaes_per_s": 2 * iters * n / (ms / 1e3) / 1e9, "ms": ms, "blocks": 2 * iters * n}
+    return {"calibration": out, "threads": n, "iters": iters}
+
+
 # ---------------------------------------------------------------- our arm
 
 def main():
@@ -351,6 +394,9 @@ def main():
 
     torch.cuda.set_device(local)
     build.build()
+    if args.calibrate_only:
+        print(json.dumps(calibrate_engines(impir)), flush=True)
+        return
     w = make_workload(args.workload, args.queries, args.record_bytes)
     N, B = w.n_records, w.record_bytes
     t_setup = time.perf_counter()
@@ -492,10 +538,29 @@ def main():
     pk, pk_kind = peaks()
     mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     blocks_per_step = sum(aes_blocks(m) for bt in batches for m in bt["ms"])
+    lookups_per_step = sum(lookups_per_query(m) for bt in batches for m in bt["ms"])
+    lookups_per_block = lookups_per_step / blocks_per_step
     launch_ms = fused_ms / max(1, fused_launches)
     achieved = blocks_per_step * args.steps / (fused_ms / 1e3) / 1e9 if fused_ms else None
-    peak = aes_peak_gaes(sms, mhz)
+    peak = smem_peak_gaes(sms, mhz, lookups_per_block)
     scan_bytes = sum(min(N, 1 << m) * B for bt in batches for m in bt["ms"])
+    # the integer-ALU form of the same bound: AES blocks x the engine's ALU-pipe instructions
+    # per block (ncu, isolated engine, scaled from its internal-node pairs to the kernel's mix
+    # of internal and leaf pairs by lookups) + one 32-bit mask-and-XOR per record word and query
+    # of the scan, over the ALU pipe's lanes x SMs x clock
+    alu = None
+    ac = alu_counts()
+    if ac and fused_ms:
+        xor_ops = sum(min(N, 1 << m) * (stride // 4) for bt in batches for m in bt["ms"])
+        per_block = ac["engine_alu_thread_inst_per_block"] * lookups_per_block / ac["engine_lookups_per_block"]
+        ops = blocks_per_step * per_block + xor_ops
+        alu_peak = sms * ac["alu_lanes_per_sm_per_clk"] * mhz * 1e6
+        alu = {"bound": "alu", "achieved": ops * args.steps / (fused_ms / 1e3) / 1e12, "peak": alu_peak / 1e12,
+               "unit": "T int-ops/s", "frac": ops * args.steps / alu_peak / (fused_ms / 1e3),
+               "ops_per_step": ops, "aes_ops_per_block": per_block, "scan_xor_ops_per_step": xor_ops,
+               "basis": f"{sms} SMs x {ac['alu_lanes_per_sm_per_clk']} ALU lanes/clk x {mhz:.0f} MHz; "
+                        f"engine {ac['engine_alu_thread_inst_per_block']:.1f} ALU ops per block "
+                        f"({ac['source']})"}
 
     # AES engine alone (same device code, no tree walk / scan): the ceiling the fused kernel
     # approaches; its lookup rate shows how close the engine runs to the shared-memory port
@@ -505,7 +570,7 @@ def main():
                                           rs.integers(0, 256, (n_cal, 16), dtype=np.uint8), 512)
     engine_gaes = 2 * 2000 * n_cal / (cal_ms / 1e3) / 1e9
     engine = {"gaes_per_s": engine_gaes,
-              "lookups_per_clk_per_sm": engine_gaes * 1e9 * 172.5 / (sms * mhz * 1e6),
+              "lookups_per_clk_per_sm": engine_gaes * 1e9 * LOOKUPS_INTERNAL_PAIR / 2 / (sms * mhz * 1e6),
               "fused_over_engine": (achieved / engine_gaes) if achieved else None,
               "note": "keyed node expansions in registers, 172.5 table lookups per block (round 1 shared)"}
 
@@ -514,7 +579,15 @@ def main():
         import oracle
         oracle.build()
         cores = os.cpu_count() or 1
-        qs = [(bi, i) for bi, bt in enumerate(batches) for i in range(bt["n"])][: args.cpu_sample]
+        # the sample takes the workload's domain sizes in turn (first unused query of each),
+        # so that its cost per query matches the workload's mix
+        by_m = {}
+        for bi, bt in enumerate(batches):
+            for i, m in enumerate(bt["ms"]):
+                by_m.setdefault(m, []).append((bi, i))
+        order = sorted(by_m)
+        qs = [by_m[order[j % len(order)]][j // len(order)] for j in range(args.cpu_sample)
+              if j // len(order) < len(by_m[order[j % len(order)]])]
         t0 = time.perf_counter()
         agree = True
         for bi, i in qs:
@@ -595,11 +668,15 @@ def main():
         rec = s32.astype("<u4").view(np.uint8).reshape(len(sub), B)
         ok = sum(int(np.array_equal(rec[i], db[a])) for i, a in enumerate(al))
         add_blocks = sum(aes_blocks(bt["ms"][i]) for bt, i in sub)
+        add_lookups = sum(lookups_per_query(bt["ms"][i], LOOKUPS_LEAF_PAIR_ADD) for bt, i in sub)
+        add_peak = smem_peak_gaes(sms, mhz, add_lookups / add_blocks)
         additive = {"queries": len(sub), "add32_queries_per_s": len(sub) / t_add, "xor_queries_per_s": len(sub) / t_xor,
                     "reconstructed_ok": ok, "launch": impir.impir_get_config_add32(dbh, len(sub)).as_dict(),
                     # same AES work as the XOR answer (one block per tree edge), wall time of one call
                     "aes_gaes_per_s": add_blocks / t_add / 1e9,
-                    "frac_of_peak": (add_blocks / t_add / 1e9 / peak) if peak else None}
+                    "frac_of_peak": add_blocks / t_add / 1e9 / add_peak,
+                    "peak_basis": f"{add_lookups / add_blocks:.2f} lookups per AES block (leaf-level pairs "
+                                  f"{LOOKUPS_LEAF_PAIR_ADD})"}
 
     # the fixed-key PRF variant (Matyas-Meyer-Oseas with two fixed AES keys: no key schedule
     # per node, but no round shared between the two children) on the largest batch, against the
@@ -639,20 +716,20 @@ def main():
         try:
             for hh in hs:
                 impir.impir_set_config(hh, **{k: cfg[k] for k in ("lane_bits", "queries_per_warp", "warps_per_cta")})
-            nq, d_keys, d_off, d_ws, wsb = big["n"], big["d_keys0"], big["d_off"], big["d_ws"], big["wsb"]
-            parts = torch.zeros((2, nq, B), dtype=torch.uint8, device="cuda")
-            whole = torch.zeros((nq, B), dtype=torch.uint8, device="cuda")
+            nb, d_keys, d_off, d_ws, wsb = big["n"], big["d_keys0"], big["d_off"], big["d_ws"], big["wsb"]
+            parts = torch.zeros((2, nb, B), dtype=torch.uint8, device="cuda")
+            whole = torch.zeros((nb, B), dtype=torch.uint8, device="cuda")
             st = torch.cuda.Stream()
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
             times = {"whole": [], "shard0": [], "shard1": [], "combine": []}
             with torch.cuda.stream(st):
                 for rep in range(3):
                     ev[0].record(st)
-                    impir.impir_answer_async(dbh, d_keys, d_off, nq, whole, d_ws, wsb, st)
+                    impir.impir_answer_async(dbh, d_keys, d_off, nb, whole, d_ws, wsb, st)
                     ev[1].record(st)
-                    impir.impir_answer_async(hs[0], d_keys, d_off, nq, parts[0], d_ws, wsb, st)
+                    impir.impir_answer_async(hs[0], d_keys, d_off, nb, parts[0], d_ws, wsb, st)
                     ev[2].record(st)
-                    impir.impir_answer_async(hs[1], d_keys, d_off, nq, parts[1], d_ws, wsb, st)
+                    impir.impir_answer_async(hs[1], d_keys, d_off, nb, parts[1], d_ws, wsb, st)
                     ev[3].record(st)
                     out = combine(parts, 0, st)
                     ev[4].record(st)
@@ -660,10 +737,10 @@ def main():
                     for name, a, b in (("whole", 0, 1), ("shard0", 1, 2), ("shard1", 2, 3), ("combine", 3, 4)):
                         times[name].append(ev[a].elapsed_time(ev[b]))
             med = {k: statistics.median(v) for k, v in times.items()}
-            row_shards = {"queries": nq, "shards": [{"row_lo": lo, "rows": n} for lo, n in blocks],
+            row_shards = {"queries": nb, "shards": [{"row_lo": lo, "rows": n} for lo, n in blocks],
                           "ms": med, "bit_identical": bool(torch.equal(out, whole)),
                           "shards_sum_over_whole": (med["shard0"] + med["shard1"]) / med["whole"],
-                          "two_gpu_projection_queries_per_s": nq / ((max(med["shard0"], med["shard1"]) + med["combine"]) / 1e3),
+                          "two_gpu_projection_queries_per_s": nb / ((max(med["shard0"], med["shard1"]) + med["combine"]) / 1e3),
                           "note": "one GPU; the projection leaves out the all-gather of 2 x Q x B bytes"}
             del parts, whole
         finally:
@@ -721,12 +798,15 @@ def main():
             "e2e": e2e,
             "gpu_launches": all_launches,
             "clocks": clocks,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GAES/s",
+            "roofline": {"bound": "smem_port", "achieved": achieved, "peak": peak, "unit": "GAES/s",
                          "frac": (achieved / peak) if achieved else None,
                          "traffic": traffic,
                          "peak_basis": f"{sms} SMs x {mhz:.0f} MHz x {SMEM_LOOKUPS_PER_CLK_PER_SM} table lookups/clk"
-                                       f" / {LOOKUPS_PER_BLOCK_KEYED} lookups per keyed AES block",
+                                       f" / {lookups_per_block:.2f} lookups per AES block (the kernel's code: "
+                                       f"{LOOKUPS_INTERNAL_PAIR} per internal node pair, {LOOKUPS_LEAF_PAIR} per "
+                                       f"leaf-level pair)",
                          "kernel": "fused_kernel", "avg_launch_ms": launch_ms, "launches": fused_launches},
+            "roofline_alu": alu,
             "scan": {"logical_gbs": scan_bytes * args.steps / (ms / 1e3) / 1e9,
                      # DRAM bytes of one fused launch (ncu capture) over its live duration
                      "physical_gbs": (traffic / (launch_ms / 1e3) / 1e9) if traffic and launch_ms else None,
