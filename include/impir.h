@@ -336,9 +336,13 @@ const char* impir_last_error(void);
  *   - It calls no cudaMalloc, cudaFree or other allocating routine.
  *   - The batch must fit: the workspace of impir_workspace_bytes(n_queries, stride_bytes)
  *     must be <= IMPIR_NOALLOC_SCRATCH_BYTES, else EINVAL and nothing is launched.
- *   - The first call on a device does a one-time set-up for that device (it looks up the
- *     scratch array's device address and uploads a 1 KiB AES table); make that first call
- *     before any stream capture.
+ *   - The first call on a device does a one-time set-up for that device: it looks up the
+ *     scratch array's device address, uploads a 1 KiB AES table, and prepares every kernel a
+ *     later call can launch (sets their shared-memory limit on that device and loads their
+ *     code, which with lazy module loading could otherwise take device memory at a later
+ *     call). Make that first call before any stream capture; later calls do no set-up work.
+ *   - The launch shape is the one impir_answer_async picks by default for the same database
+ *     size, record stride and batch size.
  *   - Every call shares the one scratch array, which keeps the last call's contents (each
  *     call clears what must start at zero). Calls whose kernels overlap on the GPU race on
  *     it: issue them on one stream, or otherwise order them.
@@ -367,6 +371,20 @@ impir_status impir_timing_read(double* fused_ms, uint64_t* fused_launches, uint6
  * (2 * iters * n_threads AES-128 blocks). Allocates and frees its own device buffers. */
 impir_status impir_aes_calibrate(int prf, uint32_t iters, uint32_t n_threads, uint32_t threads_per_cta,
                                  const uint8_t* seeds, uint8_t* out, double* ms);
+
+/* Index checks of the debug build (measurement and test support; the paper has no
+ * counterpart). A library compiled with IMPIR_BOUNDS (libimpir_bounds.so, built by
+ * `python -m paper_2509_06514_gb300.build --bounds`) compares every shared-memory, database
+ * record, key, query, schedule and accumulator index its kernels use with the extent of its
+ * buffer before the access; a failed check skips the access (a load reads zero) and is
+ * recorded per device and in the launch's workspace header. Nothing traps or waits. Its
+ * synchronous calls (impir_answer, impir_answer_add32, impir_answer_streamed) return ECUDA
+ * when a check failed during the call. This call waits for the device, then returns the
+ * number of failed checks since the last call, the site code and index of the first one
+ * (sites: 1 T-table, 2 selection-bit/node/share buffer, 3 database word, 4 key byte, 5 query
+ * index, 6 schedule, 7 accumulator word, 8 lane stack, 9 setup writes, 10 answer byte), and
+ * clears the record. EINVAL in a library built without IMPIR_BOUNDS. */
+impir_status impir_bounds_status(uint32_t* n_failed, uint32_t* first_site, uint64_t* first_index);
 
 /* Number of streaming multiprocessors of the current device (0 if none). */
 int32_t impir_device_sm_count(void);

@@ -17,7 +17,10 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libimpir.so")
+# IMPIR_BOUNDS=1 in the environment loads the debug build with index checks instead
+# (libimpir_bounds.so, from `python -m paper_2509_06514_gb300.build --bounds`).
+BOUNDS = os.environ.get("IMPIR_BOUNDS") == "1"
+LIB_PATH = os.path.join(_HERE, "libimpir_bounds.so" if BOUNDS else "libimpir.so")
 
 IMPIR_OK, IMPIR_EINVAL, IMPIR_ENOMEM, IMPIR_ECUDA, IMPIR_ETIMEOUT, IMPIR_EBUSY = range(6)
 IMPIR_PRF_AES_KEYED = 0
@@ -34,7 +37,7 @@ EXPORTS = [
     "impir_aes_calibrate", "impir_db_update", "impir_db_update_async", "impir_db_version", "impir_server_update",
     "impir_answer_streamed", "impir_answer_add32", "impir_answer_add32_async", "impir_tune_cache_save",
     "impir_tune_cache_load", "impir_db_load_rows", "impir_db_rows", "impir_combine_partials",
-    "impir_get_config_add32",
+    "impir_get_config_add32", "impir_bounds_status",
 ]
 
 
@@ -67,8 +70,9 @@ def lib():
     with _lock:
         if _lib is None:
             if not os.path.exists(LIB_PATH):
-                raise ImportError(f"libimpir.so is not built ({LIB_PATH}); run __graft_entry__.build() or "
-                                  "python -m paper_2509_06514_gb300.build")
+                raise ImportError(f"{os.path.basename(LIB_PATH)} is not built ({LIB_PATH}); run "
+                                  "__graft_entry__.build() or python -m paper_2509_06514_gb300.build"
+                                  + (" --bounds" if BOUNDS else ""))
             L = ctypes.CDLL(LIB_PATH)
             vp, u8p = ctypes.c_void_p, ctypes.c_void_p
             sig = {
@@ -128,6 +132,8 @@ def lib():
                 "impir_db_rows": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64),
                                                  ctypes.POINTER(ctypes.c_uint64)]),
                 "impir_combine_partials": (ctypes.c_int, [ctypes.c_int, vp, ctypes.c_uint32, ctypes.c_uint64, vp, vp]),
+                "impir_bounds_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                                                       ctypes.POINTER(ctypes.c_uint64)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -335,6 +341,13 @@ def impir_reconstruct(r0, r1) -> bytes:
 
 def impir_last_error() -> str:
     return lib().impir_last_error().decode(errors="replace")
+
+
+def impir_bounds_status() -> dict:
+    """Failed index checks of the debug build since the last call (waits for the device)."""
+    n, site, idx = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64()
+    _check(lib().impir_bounds_status(ctypes.byref(n), ctypes.byref(site), ctypes.byref(idx)), "impir_bounds_status")
+    return {"n_failed": n.value, "first_site": site.value, "first_index": idx.value}
 
 
 def impir_device_sm_count() -> int:

@@ -16,6 +16,9 @@ template <int PRF>
 __global__ void __launch_bounds__(512, 1) aes_bench_kernel(const __grid_constant__ FusedParams P, const uint4* seeds,
                                                            uint4* out, uint32_t iters, uint32_t n_threads) {
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+#ifdef IMPIR_BOUNDS
+    if (tid == 0) s_bctx = BoundsCtx{P.bounds, nullptr, nullptr, 0, nullptr, 0, kTableBytes, 0};
+#endif
     for (uint32_t i = tid; i < 256 * 32; i += nthr) {
         const uint32_t x = i >> 5, l = i & 31;
         const uint32_t t0 = __ldg(P.te0 + x);
@@ -73,6 +76,7 @@ extern "C" impir_status impir_aes_calibrate(int prf, uint32_t iters, uint32_t n_
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e == cudaSuccess) {
         fp.te0 = d_te0;
+        fp.bounds = bounds_record();
         const unsigned blocks = (n_threads + threads_per_cta - 1) / threads_per_cta;
         auto k = prf == 0 ? aes_bench_kernel<0> : aes_bench_kernel<1>;
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTableBytes));

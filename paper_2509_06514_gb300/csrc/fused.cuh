@@ -34,13 +34,31 @@
 // byte of a T-table entry that equals S[x] (Te2 byte 0, Te3 byte 1, Te0 byte 2, Te1 byte 3).
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 
+#include "bounds.cuh"
 #include "impir_internal.h"
 
 namespace impir {
 
 extern __shared__ __align__(16) uint8_t g_smem[];
+
+// Debug build: n bytes at p lie inside the calling warp's slice of the bit / node / share
+// buffer (and inside the launch's dynamic shared memory).
+__device__ __forceinline__ bool slice_ok(const void* p, uint32_t n) {
+#ifdef IMPIR_BOUNDS
+    const long long o = static_cast<const uint8_t*>(p) - g_smem;
+    const long long lo = kTableBytes + kSegSmemBytes + (long long)(threadIdx.x >> 5) * s_bctx.warp_slice_bytes;
+    return IMPIR_IN_BOUNDS(o >= lo && o + n <= lo + s_bctx.warp_slice_bytes && o + n <= s_bctx.smem_bytes, kSiteBits,
+                           o);
+#else
+    return true;
+#endif
+}
+
+// A 32-bit word of the warp's bit / share buffer (zero if a debug-build check fails).
+__device__ __forceinline__ uint32_t ld_slice(const uint32_t* p) { return slice_ok(p, 4) ? *p : 0u; }
 
 struct Blk {
     uint32_t x, y, z, w;
@@ -55,7 +73,9 @@ __device__ __forceinline__ uint32_t tix(uint32_t w, uint32_t lane4, int b) {
 
 template <int K>
 __device__ __forceinline__ uint32_t T(uint32_t off) {
-    return *reinterpret_cast<const uint32_t*>(g_smem + off + (K & 1) * 128 + (K >> 1) * 65536);
+    const uint32_t o = off + (K & 1) * 128 + (K >> 1) * 65536;
+    if (!IMPIR_IN_BOUNDS(o + 4 <= kTableBytes, kSiteTable, o)) return 0;
+    return *reinterpret_cast<const uint32_t*>(g_smem + o);
 }
 
 // One full round: SubBytes, ShiftRows, MixColumns, AddRoundKey (FIPS-197 §5.1).
@@ -271,17 +291,63 @@ __device__ __forceinline__ size_t cw_off(uint32_t m, uint32_t t, uint32_t x, uin
     return 8 + size_t(t) * 32 * (m + 1) + (size_t(x) * (m + 1) + d) * 16;
 }
 
+// Debug build: the n bytes at kq + off lie inside the key (domain bits m) and, when the key
+// buffer's size is known, inside the buffer.
+__device__ __forceinline__ bool key_bytes_ok(const uint8_t* kq, uint32_t m, size_t off, uint32_t n) {
+#ifdef IMPIR_BOUNDS
+    const long long rel = (kq - s_bctx.keys) + (long long)off;
+    const bool in_key = off + n <= 8 + 64ull * (m + 1);
+    const bool in_buf = rel >= 0 && (s_bctx.keys_bytes == 0 || (unsigned long long)rel + n <= s_bctx.keys_bytes);
+    return IMPIR_IN_BOUNDS(in_key && in_buf, kSiteKey, rel);
+#else
+    return true;
+#endif
+}
+
 __device__ __forceinline__ Blk cw_load(const uint8_t* kq, uint32_t m, uint32_t t, uint32_t x, uint32_t d) {
-    const uint2* p = reinterpret_cast<const uint2*>(kq + cw_off(m, t, x, d));
+    const size_t off = cw_off(m, t, x, d);
+    if (!key_bytes_ok(kq, m, off, 16)) return {0, 0, 0, 0};
+    const uint2* p = reinterpret_cast<const uint2*>(kq + off);
     const uint2 lo = __ldg(p), hi = __ldg(p + 1);
     return {lo.x, lo.y, hi.x, hi.y};
 }
 
 __device__ __forceinline__ uint32_t cw_lsb(const uint8_t* kq, uint32_t m, uint32_t t, uint32_t x, uint32_t d) {
-    return __ldg(kq + cw_off(m, t, x, d)) & 1u;
+    const size_t off = cw_off(m, t, x, d);
+    if (!key_bytes_ok(kq, m, off, 1)) return 0;
+    return __ldg(kq + off) & 1u;
 }
 
-__device__ __forceinline__ uint4 ld_db(const uint4* p) { return __ldg(p); }
+// A 16-byte database word (debug build: inside the words the launch may read, else zero).
+__device__ __forceinline__ uint4 ld_db(const uint4* p) {
+#ifdef IMPIR_BOUNDS
+    const long long w = p - s_bctx.db;
+    if (!IMPIR_IN_BOUNDS(w >= 0 && (unsigned long long)w < s_bctx.db_words, kSiteRecord, w)) return make_uint4(0, 0, 0, 0);
+#endif
+    return __ldg(p);
+}
+
+// Index of the q-th query of a group whose sorted query indices start at qidx (debug build:
+// the position lies inside the sorted permutation and the index names a query of the batch).
+__device__ __forceinline__ uint32_t query_at(const FusedParams& P, const uint32_t* qidx, uint32_t q) {
+#ifdef IMPIR_BOUNDS
+    const long long i = (qidx - reinterpret_cast<const uint32_t*>(P.ws + P.lay.off_perm)) + (long long)q;
+    if (!IMPIR_IN_BOUNDS(i >= 0 && i < (long long)P.n_queries, kSiteQuery, i)) return 0;
+    const uint32_t v = qidx[q];
+    if (!IMPIR_IN_BOUNDS(v < P.n_queries, kSiteQuery, v)) return 0;
+    return v;
+#else
+    return qidx[q];
+#endif
+}
+
+// The wire key of query qi (debug build: its header lies inside the key buffer when the size
+// of that is known).
+__device__ __forceinline__ const uint8_t* query_key(const FusedParams& P, uint32_t qi) {
+    const uint32_t off = P.key_off[qi];
+    if (!IMPIR_IN_BOUNDS(P.keys_bytes == 0 || off + 8ull <= P.keys_bytes, kSiteKey, off)) return P.keys;
+    return P.keys + off;
+}
 
 __device__ __forceinline__ void mad4(uint4& a, const uint4 v, uint32_t s) {
     a.x += v.x * s;
@@ -300,6 +366,12 @@ __device__ __forceinline__ void red_add(uint4* dst, const uint4 v) {
     if (v.y) atomicAdd(d + 1, v.y);
     if (v.z) atomicAdd(d + 2, v.z);
     if (v.w) atomicAdd(d + 3, v.w);
+}
+
+// Adds v into word k of query qi's accumulator (debug build: both inside the batch's answers).
+__device__ __forceinline__ void acc_add(const FusedParams& P, uint4* acc_out, uint32_t qi, uint32_t k, const uint4 v) {
+    if (!IMPIR_IN_BOUNDS(qi < P.n_queries && k < P.words, kSiteAcc, (unsigned long long)qi * P.words + k)) return;
+    red_add(acc_out + size_t(qi) * P.words + k, v);
 }
 
 // Additive answer of one chunk of a warp tile for the unit's queries: acc_q += share_q * D[r],
@@ -342,7 +414,7 @@ __device__ __forceinline__ void scan_chunk_add(const FusedParams& P, uint64_t ti
                     if (on && r < n)
 #pragma unroll
                         for (int q = 0; q < QC; ++q)
-                            if (uint32_t(q) < count) mad4(acc[q], v[u], vl[q * qstride + r]);
+                            if (uint32_t(q) < count) mad4(acc[q], v[u], ld_slice(&vl[q * qstride + r]));
                 }
             }
         }
@@ -357,11 +429,11 @@ __device__ __forceinline__ void scan_chunk_add(const FusedParams& P, uint64_t ti
             if (lr == 0)
 #pragma unroll
                 for (int q = 0; q < QC; ++q)
-                    if (uint32_t(q) < count) red_add(acc_out + size_t(qidx[q]) * W + lk, acc[q]);
+                    if (uint32_t(q) < count) acc_add(P, acc_out, query_at(P, qidx, q), lk, acc[q]);
         } else if (on) {
 #pragma unroll
             for (int q = 0; q < QC; ++q)
-                if (uint32_t(q) < count) red_add(acc_out + size_t(qidx[q]) * W + lk, acc[q]);
+                if (uint32_t(q) < count) acc_add(P, acc_out, query_at(P, qidx, q), lk, acc[q]);
         }
     } else {
         // W > 32: the whole warp reads one record per step, NK words per lane, in column passes
@@ -388,7 +460,7 @@ __device__ __forceinline__ void scan_chunk_add(const FusedParams& P, uint64_t ti
 #pragma unroll
                     for (int q = 0; q < QC; ++q)
                         if (uint32_t(q) < count) {
-                            const uint32_t sv = vl[q * qstride + r];
+                            const uint32_t sv = ld_slice(&vl[q * qstride + r]);
 #pragma unroll
                             for (int c = 0; c < NK; ++c) mad4(acc[q][c], v[c], sv);
                         }
@@ -400,7 +472,7 @@ __device__ __forceinline__ void scan_chunk_add(const FusedParams& P, uint64_t ti
 #pragma unroll
                     for (int c = 0; c < NK; ++c) {
                         const uint32_t k = k0 + lane + 32 * c;
-                        if (k < W) red_add(acc_out + size_t(qidx[q]) * W + k, acc[q][c]);
+                        if (k < W) acc_add(P, acc_out, query_at(P, qidx, q), k, acc[q][c]);
                     }
         }
     }
@@ -431,7 +503,7 @@ __device__ __forceinline__ void lane_eval(const FusedParams& P, const uint8_t* k
                                           const Blk start, uint32_t d0) {
     Blk node = walk_down<PRF>(P, kq, m, D, sub, L, start, d0);
     if (sq == 0) {
-        atomicOr(&bits[lane >> 5], (node.x & 1u) << (lane & 31));
+        if (slice_ok(&bits[lane >> 5], 4)) atomicOr(&bits[lane >> 5], (node.x & 1u) << (lane & 31));
         return;
     }
     Blk stk[kMaxLaneBits];
@@ -445,12 +517,13 @@ __device__ __forceinline__ void lane_eval(const FusedParams& P, const uint8_t* k
             acc |= b2 << ((2 * p) & 31);
             ++p;
             if (sq >= 5 && (p & 15) == 0) {
-                bits[(lane << (sq - 5)) + ((p - 1) >> 4)] = acc;
+                uint32_t* w = &bits[(lane << (sq - 5)) + ((p - 1) >> 4)];
+                if (slice_ok(w, 4)) *w = acc;
                 acc = 0;
             }
             if (p == npairs) break;
             depth = m - 1 - (__ffs(int(p)) - 1);
-            node = stk[depth - D];
+            if (IMPIR_IN_BOUNDS(depth - D < kMaxLaneBits, kSiteStack, depth - D)) node = stk[depth - D];
         } else {
             const Blk c0 = cw_load(kq, m, t, 0, depth + 1);
             const Blk c1 = cw_load(kq, m, t, 1, depth + 1);
@@ -460,11 +533,11 @@ __device__ __forceinline__ void lane_eval(const FusedParams& P, const uint8_t* k
             else
                 mmo_pair(node, L, P.mmo_rk, c0, c1, a, b);
             ++depth;
-            stk[depth - D] = b;
+            if (IMPIR_IN_BOUNDS(depth - D < kMaxLaneBits, kSiteStack, depth - D)) stk[depth - D] = b;
             node = a;
         }
     }
-    if (sq < 5) atomicOr(&bits[(lane << sq) >> 5], acc << ((lane << sq) & 31));
+    if (sq < 5 && slice_ok(&bits[(lane << sq) >> 5], 4)) atomicOr(&bits[(lane << sq) >> 5], acc << ((lane << sq) & 31));
 }
 
 // ---- additive answer (MODE 1) ----
@@ -497,12 +570,14 @@ __device__ __forceinline__ void add_walk_chunk(const FusedParams& P, const uint8
             wa ^= cw_load(kq, m, t, 0, m).x;
             wb ^= cw_load(kq, m, t, 1, m).x;
             const uint32_t r = lane * ch + ((2 * p) & (ch - 1));
-            shares[r] = (wa ^ neg) - neg;
-            shares[r + 1] = (wb ^ neg) - neg;
+            if (slice_ok(&shares[r], 8)) {
+                shares[r] = (wa ^ neg) - neg;
+                shares[r + 1] = (wb ^ neg) - neg;
+            }
             ++p;
             if (p == npairs) break;
             depth = m - 1 - (__ffs(int(p)) - 1);
-            node = w.stk[depth - D];
+            if (IMPIR_IN_BOUNDS(depth - D < kMaxLaneBits, kSiteStack, depth - D)) node = w.stk[depth - D];
             if (p == end) break;
         } else {
             const Blk c0 = cw_load(kq, m, t, 0, depth + 1);
@@ -513,7 +588,7 @@ __device__ __forceinline__ void add_walk_chunk(const FusedParams& P, const uint8
             else
                 mmo_pair(node, L, P.mmo_rk, c0, c1, a, b);
             ++depth;
-            w.stk[depth - D] = b;
+            if (IMPIR_IN_BOUNDS(depth - D < kMaxLaneBits, kSiteStack, depth - D)) w.stk[depth - D] = b;
             node = a;
         }
     }
@@ -541,7 +616,7 @@ __device__ __forceinline__ void unit_add(const FusedParams& P, const GroupDesc& 
     for (int q = 0; q < QC; ++q) {
         neg[q] = 0;
         if (uint32_t(q) < count) {
-            const uint8_t* kq = P.keys + P.key_off[qidx[q]];
+            const uint8_t* kq = query_key(P, query_at(P, qidx, q));
             const Blk start{__shfl_sync(0xffffffffu, top.x, q), __shfl_sync(0xffffffffu, top.y, q),
                             __shfl_sync(0xffffffffu, top.z, q), __shfl_sync(0xffffffffu, top.w, q)};
             w[q].node = kq[1] == 0 ? walk_down<0>(P, kq, m, D, sub, L, start, Dt)
@@ -554,7 +629,8 @@ __device__ __forceinline__ void unit_add(const FusedParams& P, const GroupDesc& 
     if (sq == 0) {  // one leaf per lane: the subtree root is the leaf
 #pragma unroll
         for (int q = 0; q < QC; ++q)
-            if (uint32_t(q) < count) shares[q * qstride + lane] = (w[q].node.x ^ neg[q]) - neg[q];
+            if (uint32_t(q) < count && slice_ok(&shares[q * qstride + lane], 4))
+                shares[q * qstride + lane] = (w[q].node.x ^ neg[q]) - neg[q];
         __syncwarp();
         scan_chunk_add<QC, NK>(P, tile_base, nrec, shares, qstride, count, qidx, 1, 32, 0, 0, acc_out, lane);
         return;
@@ -567,7 +643,7 @@ __device__ __forceinline__ void unit_add(const FusedParams& P, const GroupDesc& 
 #pragma unroll
         for (int q = 0; q < QC; ++q)
             if (uint32_t(q) < count) {
-                const uint8_t* kq = P.keys + P.key_off[qidx[q]];
+                const uint8_t* kq = query_key(P, query_at(P, qidx, q));
                 if (kq[1] == 0)
                     add_walk_chunk<0>(P, kq, m, D, sq, w[q], ch, shares + q * qstride, lane, L, neg[q]);
                 else
@@ -587,6 +663,12 @@ __device__ __forceinline__ void red_xor(uint4* dst, const uint4 v) {
     if (v.z | v.w)
         atomicXor(reinterpret_cast<unsigned long long*>(dst) + 1,
                   (unsigned long long)v.z | ((unsigned long long)v.w << 32));
+}
+
+// XORs v into word k of query qi's accumulator (debug build: both inside the batch's answers).
+__device__ __forceinline__ void acc_xor(const FusedParams& P, uint4* acc_out, uint32_t qi, uint32_t k, const uint4 v) {
+    if (!IMPIR_IN_BOUNDS(qi < P.n_queries && k < P.words, kSiteAcc, (unsigned long long)qi * P.words + k)) return;
+    red_xor(acc_out + size_t(qi) * P.words + k, v);
 }
 
 __device__ __forceinline__ void xor_masked(uint4& a, const uint4 v, uint32_t msk) {
@@ -628,7 +710,7 @@ __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_ba
         for (uint32_t c0 = 0; c0 < nrec; c0 += 32) {
             uint32_t sel[QC];
 #pragma unroll
-            for (int q = 0; q < QC; ++q) sel[q] = bits[q * bw + (c0 >> 5)] >> lr;  // bit i*R of sel: record c0+i*R+lr
+            for (int q = 0; q < QC; ++q) sel[q] = ld_slice(&bits[q * bw + (c0 >> 5)]) >> lr;  // bit i*R: record c0+i*R+lr
             const uint32_t nloc = min(32u, nrec - c0);
             if (R == 1) {
                 // one record per step for the whole warp: its selection bits are warp-uniform
@@ -671,11 +753,11 @@ __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_ba
             if (lr == 0)
 #pragma unroll
                 for (int q = 0; q < QC; ++q)
-                    if (uint32_t(q) < count) red_xor(acc_out + size_t(qidx[q]) * W + lk, acc[q]);
+                    if (uint32_t(q) < count) acc_xor(P, acc_out, query_at(P, qidx, q), lk, acc[q]);
         } else if (on) {
 #pragma unroll
             for (int q = 0; q < QC; ++q)
-                if (uint32_t(q) < count) red_xor(acc_out + size_t(qidx[q]) * W + lk, acc[q]);
+                if (uint32_t(q) < count) acc_xor(P, acc_out, query_at(P, qidx, q), lk, acc[q]);
         }
     } else {
         // W > 32: the whole warp reads one record per step, NK words per lane, in column
@@ -689,7 +771,7 @@ __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_ba
             for (uint32_t c0 = 0; c0 < nrec; c0 += 32) {
                 uint32_t sel[QC];
 #pragma unroll
-                for (int q = 0; q < QC; ++q) sel[q] = bits[q * bw + (c0 >> 5)];
+                for (int q = 0; q < QC; ++q) sel[q] = ld_slice(&bits[q * bw + (c0 >> 5)]);
                 const uint32_t nloc = min(32u, nrec - c0);
                 // RB records' loads in flight before their XORs (fewer for the widest records,
                 // whose loads already fill the registers)
@@ -720,7 +802,7 @@ __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_ba
 #pragma unroll
                     for (int c = 0; c < NK; ++c) {
                         const uint32_t k = k0 + lane + 32 * c;
-                        if (k < W) red_xor(acc_out + size_t(qidx[q]) * W + k, acc[q][c]);
+                        if (k < W) acc_xor(P, acc_out, query_at(P, qidx, q), k, acc[q][c]);
                     }
         }
     }
@@ -749,8 +831,22 @@ __global__ void __launch_bounds__((NK == 1 && QC <= 8) ? 640 : 512, 1)
         rb[32 + l] = __funnelshift_l(t0, t0, 24);
     }
     WsHeader* hdr = reinterpret_cast<WsHeader*>(P.ws);
+#ifdef IMPIR_BOUNDS
+    if (tid == 0) {
+        s_bctx.rec = P.bounds;
+        s_bctx.hdr = hdr;
+        s_bctx.keys = P.keys;
+        s_bctx.keys_bytes = P.keys_bytes;
+        s_bctx.db = P.db;
+        s_bctx.db_words = P.db_words;
+        s_bctx.smem_bytes = P.smem_bytes;
+        s_bctx.warp_slice_bytes = QC * P.bits_words * 4;
+    }
+    __syncthreads();
+#endif
     SegDesc* segs = reinterpret_cast<SegDesc*>(g_smem + kTableBytes);
-    const uint32_t n_segs = hdr->n_segs;
+    uint32_t n_segs = hdr->n_segs;
+    if (!IMPIR_IN_BOUNDS(n_segs <= kMaxSegments, kSiteSchedule, n_segs)) n_segs = kMaxSegments;
     const SegDesc* gsegs = reinterpret_cast<const SegDesc*>(P.ws + P.lay.off_segs);
     for (uint32_t i = tid; i < n_segs; i += nthr) segs[i] = gsegs[i];
     __syncthreads();
@@ -771,7 +867,9 @@ __global__ void __launch_bounds__((NK == 1 && QC <= 8) ? 640 : 512, 1)
         while (j + 1 < n_segs && segs[j + 1].unit_lo <= u) ++j;
         const unsigned long long off = u - segs[j].unit_lo;
         const unsigned long long tile = segs[j].tile_lo + off / segs[j].count;
-        const GroupDesc gd = groups[uint32_t(off % segs[j].count)];
+        const uint32_t gi = uint32_t(off % segs[j].count);
+        if (!IMPIR_IN_BOUNDS(gi < hdr->n_groups, kSiteSchedule, gi)) continue;
+        const GroupDesc gd = groups[gi];
 
         const uint32_t m = gd.m;
         const uint32_t sq = m >= 5 ? min(P.lane_bits, m - 5) : 0u;
@@ -794,7 +892,8 @@ __global__ void __launch_bounds__((NK == 1 && QC <= 8) ? 640 : 512, 1)
         const bool coop = MODE == 0 && QC <= 8 && P.bits_words >= 64 && m >= 5;
         if (MODE == 0 && !coop) {
             for (int q = 0; q < QC; ++q)
-                for (uint32_t w = lane; w < nwords; w += 32) bits[q * P.bits_words + w] = 0;
+                for (uint32_t w = lane; w < nwords; w += 32)
+                    if (slice_ok(&bits[q * P.bits_words + w], 4)) bits[q * P.bits_words + w] = 0;
         }
         __syncwarp();
         const uint32_t* qidx = perm + gd.first;
@@ -804,7 +903,7 @@ __global__ void __launch_bounds__((NK == 1 && QC <= 8) ? 640 : 512, 1)
         const uint32_t Dt = D > 5 ? D - 5 : 0;
         Blk top{0, 0, 0, 0};
         if (lane < gd.count) {
-            const uint8_t* kq = P.keys + P.key_off[qidx[lane]];
+            const uint8_t* kq = query_key(P, query_at(P, qidx, lane));
             top = cw_load(kq, m, 0, 0, 0);  // R(0,0) = C_0[0][0], Eq. (2)
             for (uint32_t d = 1; d <= Dt; ++d) {
                 const uint32_t x = uint32_t(tile >> (Dt - d)) & 1u;
@@ -820,7 +919,8 @@ __global__ void __launch_bounds__((NK == 1 && QC <= 8) ? 640 : 512, 1)
         if (coop) {
             uint8_t* nodes = reinterpret_cast<uint8_t*>(bits);  // query q's nodes at q * slot
             const uint32_t slot = P.bits_words * 4;
-            if (lane < gd.count) *reinterpret_cast<uint4*>(nodes + lane * slot) = make_uint4(top.x, top.y, top.z, top.w);
+            if (lane < gd.count && slice_ok(nodes + lane * slot, 16))
+                *reinterpret_cast<uint4*>(nodes + lane * slot) = make_uint4(top.x, top.y, top.z, top.w);
             __syncwarp();
             for (uint32_t k = 0; k < 4; ++k) {  // level k -> k + 1 below the warp-tile root
                 const uint32_t per = 1u << k, items = gd.count * per;
@@ -831,10 +931,11 @@ __global__ void __launch_bounds__((NK == 1 && QC <= 8) ? 640 : 512, 1)
                     const bool act = f < items;
                     const uint32_t q = act ? f % gd.count : 0, i = act ? (per - 1) - f / gd.count : 0;
                     uint4 pv = make_uint4(0, 0, 0, 0);
-                    if (act) pv = *reinterpret_cast<const uint4*>(nodes + q * slot + i * 16);
+                    if (act && slice_ok(nodes + q * slot + i * 16, 16))
+                        pv = *reinterpret_cast<const uint4*>(nodes + q * slot + i * 16);
                     __syncwarp();
                     if (act) {
-                        const uint8_t* kq = P.keys + P.key_off[qidx[q]];
+                        const uint8_t* kq = query_key(P, query_at(P, qidx, q));
                         const Blk par{pv.x, pv.y, pv.z, pv.w};
                         const uint32_t t = par.x & 1u, d = Dt + k + 1;
                         const Blk c0 = cw_load(kq, m, t, 0, d), c1 = cw_load(kq, m, t, 1, d);
@@ -843,19 +944,24 @@ __global__ void __launch_bounds__((NK == 1 && QC <= 8) ? 640 : 512, 1)
                             keyed_pair(par, L, c0, c1, a, b);
                         else
                             mmo_pair(par, L, P.mmo_rk, c0, c1, a, b);
-                        *reinterpret_cast<uint4*>(nodes + q * slot + (2 * i) * 16) = make_uint4(a.x, a.y, a.z, a.w);
-                        *reinterpret_cast<uint4*>(nodes + q * slot + (2 * i + 1) * 16) = make_uint4(b.x, b.y, b.z, b.w);
+                        if (slice_ok(nodes + q * slot + (2 * i) * 16, 32)) {
+                            *reinterpret_cast<uint4*>(nodes + q * slot + (2 * i) * 16) = make_uint4(a.x, a.y, a.z, a.w);
+                            *reinterpret_cast<uint4*>(nodes + q * slot + (2 * i + 1) * 16) = make_uint4(b.x, b.y, b.z, b.w);
+                        }
                     }
                     __syncwarp();
                 }
             }
             for (uint32_t qi = 0; qi < gd.count; ++qi) {
-                const uint8_t* kq = P.keys + P.key_off[qidx[qi]];
+                const uint8_t* kq = query_key(P, query_at(P, qidx, qi));
                 const uint32_t prf = kq[1];
                 // lane l's parent at level 4 is node l >> 1; its subtree root is child l & 1
-                const uint4 pv = *reinterpret_cast<const uint4*>(nodes + qi * slot + (lane >> 1) * 16);
+                uint4 pv = make_uint4(0, 0, 0, 0);
+                if (slice_ok(nodes + qi * slot + (lane >> 1) * 16, 16))
+                    pv = *reinterpret_cast<const uint4*>(nodes + qi * slot + (lane >> 1) * 16);
                 __syncwarp();
-                for (uint32_t w = lane; w < nwords; w += 32) bits[qi * P.bits_words + w] = 0;
+                for (uint32_t w = lane; w < nwords; w += 32)
+                    if (slice_ok(&bits[qi * P.bits_words + w], 4)) bits[qi * P.bits_words + w] = 0;
                 __syncwarp();
                 const Blk start{pv.x, pv.y, pv.z, pv.w};
                 if (lane_on) {
@@ -867,7 +973,7 @@ __global__ void __launch_bounds__((NK == 1 && QC <= 8) ? 640 : 512, 1)
             }
         } else {
             for (uint32_t qi = 0; qi < gd.count; ++qi) {
-                const uint8_t* kq = P.keys + P.key_off[qidx[qi]];
+                const uint8_t* kq = query_key(P, query_at(P, qidx, qi));
                 const uint32_t prf = kq[1];
                 const Blk start{__shfl_sync(0xffffffffu, top.x, qi), __shfl_sync(0xffffffffu, top.y, qi),
                                 __shfl_sync(0xffffffffu, top.z, qi), __shfl_sync(0xffffffffu, top.w, qi)};
@@ -885,11 +991,32 @@ __global__ void __launch_bounds__((NK == 1 && QC <= 8) ? 640 : 512, 1)
     }
 }
 
-// Sets the dynamic shared memory limit once and launches one instantiation.
+// Sets the dynamic shared-memory limit of one instantiation on the current device. The attribute
+// belongs to the device, so it is set once per device (a bit per device below 64; devices
+// beyond that set it at every call); setting it also loads the kernel's code on that device.
+template <int QC, int NK, int MODE = 0>
+cudaError_t prepare_fused_t() {
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev >= 0 && dev < 64 ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    // the block's limit less the kernel's static shared memory (none, except the debug build's
+    // check context)
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fused_kernel<QC, NK, MODE>);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fused_kernel<QC, NK, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(kSmemMax - fa.sharedSizeBytes));
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
+// Launches one instantiation (after setting its shared-memory limit on this device).
 template <int QC, int NK, int MODE = 0>
 cudaError_t launch_fused_t(dim3 grid, dim3 block, size_t smem, cudaStream_t s, const FusedParams& p) {
-    static const cudaError_t attr = cudaFuncSetAttribute(fused_kernel<QC, NK, MODE>,
-                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    const cudaError_t attr = prepare_fused_t<QC, NK, MODE>();
     if (attr != cudaSuccess) return attr;
     fused_kernel<QC, NK, MODE><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();

@@ -13,4 +13,13 @@ cudaError_t launch_fused_q1(uint32_t nk, dim3 grid, dim3 block, size_t smem, cud
     }
 }
 
+cudaError_t prepare_fused_q1() {
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = prepare_fused_t<1, 1>();
+    if (e == cudaSuccess) e = prepare_fused_t<1, 2>();
+    if (e == cudaSuccess) e = prepare_fused_t<1, 4>();
+    if (e == cudaSuccess) e = prepare_fused_t<1, 8>();
+    return e;
+}
+
 }  // namespace impir

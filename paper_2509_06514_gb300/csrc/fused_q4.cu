@@ -8,9 +8,16 @@ cudaError_t launch_fused_q4(uint32_t nk, dim3 grid, dim3 block, size_t smem, cud
         case 1: return launch_fused_t<4, 1>(grid, block, smem, s, p);
         case 2: return launch_fused_t<4, 2>(grid, block, smem, s, p);
         case 4: return launch_fused_t<4, 4>(grid, block, smem, s, p);
-
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t prepare_fused_q4() {
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = prepare_fused_t<4, 1>();
+    if (e == cudaSuccess) e = prepare_fused_t<4, 2>();
+    if (e == cudaSuccess) e = prepare_fused_t<4, 4>();
+    return e;
 }
 
 }  // namespace impir

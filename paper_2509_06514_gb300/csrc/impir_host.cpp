@@ -123,33 +123,7 @@ int32_t add_db(const Db& d) {
     return int32_t(g_dbs.size());
 }
 
-// ---- configuration ----
-// uint4 words per lane and pass that cover a record in one pass (1, 2, 4 or 8)
-uint32_t nk_need(uint32_t words) {
-    if (words <= 32) return 1;
-    const uint32_t need = (words + 31) / 32;
-    return need <= 2 ? 2 : need <= 4 ? 4 : 8;
-}
-
-// uint4 words per lane and pass of the XOR scan for qpw queries per warp: records above 512 B
-// are scanned in column passes of nk words per lane, with qpw * nk <= 16 accumulators per lane,
-// so that more queries share every tile read (records of 1 KiB: one pass at 8 queries per warp;
-// 4 KiB: four)
-uint32_t nk_xor(uint32_t words, uint32_t qpw) {
-    if (words <= 32) return 1;
-    return std::min(nk_need(words), std::max(2u, 16u / qpw));
-}
-
-// Widest CTA the fused kernel is built for (its launch bounds): 20 warps for the XOR answer
-// with one column pass (records of at most 512 bytes) and at most 8 queries per warp, else 16.
-uint32_t max_warps(uint32_t qpw, uint32_t words) { return nk_need(words) == 1 && qpw <= 8 ? 20u : 16u; }
-
-size_t smem_for(const impir_config& c) {
-    return kTableBytes + kSegSmemBytes + size_t(c.warps_per_cta) * c.queries_per_warp * (size_t(1) << c.lane_bits) * 4;
-}
-
-constexpr size_t kSmemMax = 227 * 1024;
-
+// ---- configuration (launch-shape helpers shared with the no-alloc path: impir_internal.h) ----
 size_t smem_add(const impir_config& c);
 
 // mode 0: the XOR answer's kernels; mode 1: the additive answer's (after add_config)
@@ -167,39 +141,6 @@ impir_status check_config(const impir_config& c, uint32_t words, int mode = 0) {
     const size_t smem = mode == 0 ? smem_for(c) : smem_add(c);
     if (smem > kSmemMax) return fail(IMPIR_EINVAL, "configuration needs %zu bytes of shared memory", smem);
     return IMPIR_OK;
-}
-
-// Largest lane_bits that keeps enough warp tiles for every warp of the grid busy.
-impir_config default_config_warps(uint64_t n_records, uint32_t words, uint32_t n_queries, int sms, uint32_t warps) {
-    impir_config c{};
-    c.warps_per_cta = warps;
-    c.queries_per_launch = 0;
-    uint32_t qpw = 8;
-    while (qpw > 1 && (qpw * nk_xor(words, qpw) > 16 || qpw > n_queries)) qpw >>= 1;
-    c.queries_per_warp = qpw;
-    const double all_warps = double(sms) * c.warps_per_cta;
-    const double groups = std::ceil(double(n_queries) / qpw);
-    c.lane_bits = 0;
-    for (uint32_t s = kMaxLaneBits; s + 1 > 0; --s) {
-        impir_config t = c;
-        t.lane_bits = s;
-        if (smem_for(t) > kSmemMax) continue;
-        const double tiles = std::ceil(double(n_records) / double(32ull << s));
-        if (groups * tiles >= 3.0 * all_warps || s == 0) {
-            c.lane_bits = s;
-            break;
-        }
-    }
-    if (c.lane_bits > 8) c.lane_bits = 8;
-    return c;
-}
-
-// 20 warps per CTA where the kernel allows it and the lane subtrees stay as large as with 16.
-impir_config default_config(uint64_t n_records, uint32_t words, uint32_t n_queries, int sms) {
-    const impir_config c16 = default_config_warps(n_records, words, n_queries, sms, 16);
-    if (max_warps(c16.queries_per_warp, words) < 20) return c16;
-    const impir_config c20 = default_config_warps(n_records, words, n_queries, sms, 20);
-    return c20.lane_bits == c16.lane_bits && c20.queries_per_warp == c16.queries_per_warp ? c20 : c16;
 }
 
 impir_config config_for(const Db& db, uint32_t n_queries, int sms) {
@@ -229,6 +170,35 @@ impir_status parse_host_keys(const uint8_t* keys, uint32_t n, std::vector<uint32
         o += impir_key_bytes(m);
     }
     total = o;
+    return IMPIR_OK;
+}
+
+// ---- index checks of the debug build ----
+
+// Reads and clears the current device's record of failed index checks (the caller has waited
+// for the launches it wants covered). Without IMPIR_BOUNDS: EINVAL.
+impir_status bounds_take(uint32_t* n_failed, uint32_t* site, uint64_t* index) {
+    BoundsRecord* rec = bounds_record();
+    if (!rec) return fail(IMPIR_EINVAL, "the library was built without IMPIR_BOUNDS");
+    BoundsRecord h{}, zero{};
+    CK(cudaDeviceSynchronize(), "wait for the device");
+    CK(cudaMemcpy(&h, rec, sizeof h, cudaMemcpyDeviceToHost), "bounds record read");
+    CK(cudaMemcpy(rec, &zero, sizeof zero, cudaMemcpyHostToDevice), "bounds record clear");
+    if (n_failed) *n_failed = h.n_failed;
+    if (site) *site = h.first_site;
+    if (index) *index = h.first_index;
+    return IMPIR_OK;
+}
+
+// Synchronous calls of the debug build end here: an error if any index check failed.
+impir_status bounds_verdict() {
+#ifdef IMPIR_BOUNDS
+    uint32_t n = 0, site = 0;
+    uint64_t idx = 0;
+    if (impir_status s = bounds_take(&n, &site, &idx)) return s;
+    if (n) return fail(IMPIR_ECUDA, "%u index checks failed; the first at site %u, index %llu", n, site,
+                       (unsigned long long)idx);
+#endif
     return IMPIR_OK;
 }
 
@@ -297,9 +267,11 @@ size_t smem_add(const impir_config& c) {
     return kTableBytes + kSegSmemBytes + size_t(c.warps_per_cta) * c.queries_per_warp * add_share_words(c) * 4;
 }
 
+// keys_bytes: size of the key buffer when the library knows it (0: unknown; only the debug
+// build's index checks use it)
 impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_config& cfg, const uint8_t* d_keys,
                           const uint32_t* d_off, uint32_t n, uint8_t* d_out, uint8_t* d_ws, cudaStream_t st,
-                          int mode = 0) {
+                          int mode = 0, size_t keys_bytes = 0) {
     const WsLayout lay = ws_layout(n, db.stride);
     // a row shard covers the warp tiles of its rows (shard bounds are whole tiles) of a
     // database of n_total records; its device rows start at global row row_lo
@@ -317,6 +289,8 @@ impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_conf
     sp.qpw = cfg.queries_per_warp;
     sp.tile_lo = shard ? db.row_lo / T : 0;
     sp.tile_hi = shard ? (db.row_lo + db.n + T - 1) / T : 0;
+    sp.bounds = bounds_record();
+    sp.keys_bytes = keys_bytes;
     CK(launch_setup(sp, st), "setup kernel launch");
 
     FusedParams fp{};
@@ -334,6 +308,10 @@ impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_conf
     fp.rec_lo = db.row_lo;
     std::memcpy(fp.mmo_rk, dev.mmo_rk, sizeof fp.mmo_rk);
     const size_t smem = mode == 0 ? smem_for(cfg) : smem_add(cfg);
+    fp.bounds = sp.bounds;
+    fp.db_words = bounds_db_words(db.n * (db.stride / 16), db.stride / 16);
+    fp.keys_bytes = keys_bytes;
+    fp.smem_bytes = uint32_t(smem);
     const bool timed = timing_on();
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (timed) {
@@ -368,6 +346,7 @@ impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_conf
     zp.n_queries = n;
     zp.record_bytes = db.bytes;
     zp.stride = db.stride;
+    zp.bounds = sp.bounds;
     CK(launch_finalize(zp, st), "finalize kernel launch");
     return IMPIR_OK;
 }
@@ -376,7 +355,7 @@ impir_status launch_batch(const DeviceState& dev, const Db& db, const impir_conf
 // launch for the batch only), where the synchronous path downloads them from
 impir_status answer_async_impl(const Db& db, const impir_config* cfg_in, const uint8_t* d_keys, const uint32_t* d_off,
                                uint32_t n, uint8_t* d_out, void* d_ws, size_t ws_bytes, cudaStream_t st, int mode = 0,
-                               bool direct_out = false) {
+                               bool direct_out = false, size_t keys_bytes = 0) {
     DeviceState* dev = nullptr;
     if (impir_status s = need_device(&dev)) return s;
     if (n == 0) return IMPIR_OK;
@@ -396,7 +375,7 @@ impir_status answer_async_impl(const Db& db, const impir_config* cfg_in, const u
         if (ws_bytes < ws_layout(1, db.stride).total) return fail(IMPIR_ENOMEM, "workspace too small");
         for (uint32_t q = 0; q < n; ++q)
             if (impir_status s = launch_batch(*dev, db, cfg, d_keys, d_off + q, 1, d_out + size_t(q) * db.bytes,
-                                              static_cast<uint8_t*>(d_ws), st, mode))
+                                              static_cast<uint8_t*>(d_ws), st, mode, keys_bytes))
                 return s;
         return IMPIR_OK;
     }
@@ -404,7 +383,7 @@ impir_status answer_async_impl(const Db& db, const impir_config* cfg_in, const u
         return fail(IMPIR_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed", ws_bytes,
                     ws_layout(n, db.stride).total);
     return launch_batch(*dev, db, cfg, d_keys, d_off, n, direct_out ? nullptr : d_out, static_cast<uint8_t*>(d_ws), st,
-                        mode);
+                        mode, keys_bytes);
 }
 
 // ---- synchronous path context: cached device and pinned buffers ----
@@ -507,6 +486,10 @@ impir_status impir_timing_read(double* fused_ms, uint64_t* fused_launches, uint6
     if (fused_launches) *fused_launches = g_timing.fused;
     if (all_launches) *all_launches = g_timing.all;
     return IMPIR_OK;
+}
+
+impir_status impir_bounds_status(uint32_t* n_failed, uint32_t* first_site, uint64_t* first_index) {
+    return bounds_take(n_failed, first_site, first_index);
 }
 
 int32_t impir_device_sm_count(void) {
@@ -716,13 +699,13 @@ static impir_status answer_sync(int32_t h, const uint8_t* keys, uint32_t n, uint
     CK(cudaMemcpyAsync(d_keys, g_sync.h_stage, up, cudaMemcpyHostToDevice, st), "key upload");
     if (impir_status s = answer_async_impl(db, &cfg, d_keys, reinterpret_cast<const uint32_t*>(d_keys + koff), n,
                                            static_cast<uint8_t*>(g_sync.d_out), g_sync.d_ws, g_sync.c_ws, st, mode,
-                                           direct))
+                                           direct, total))
         return s;
     const void* src = direct ? static_cast<const void*>(static_cast<uint8_t*>(g_sync.d_ws) + lay.off_acc) : g_sync.d_out;
     CK(cudaMemcpyAsync(g_sync.h_stage, src, out_bytes, cudaMemcpyDeviceToHost, st), "answer download");
     CK(cudaStreamSynchronize(st), "answer");
     std::memcpy(out, g_sync.h_stage, out_bytes);
-    return IMPIR_OK;
+    return bounds_verdict();
 }
 
 impir_status impir_answer(int32_t h, const uint8_t* keys, uint32_t n, uint8_t* out) {
@@ -936,6 +919,8 @@ impir_status impir_answer_streamed(const void* records, uint64_t N, uint32_t B, 
         sp.tile_lo = lo / T;
         sp.tile_hi = (lo + cnt + T - 1) / T;
         sp.keep_acc = c > 0;
+        sp.bounds = bounds_record();
+        sp.keys_bytes = total;
         e = launch_setup(sp, ks[b]);
         if (e == cudaSuccess && c == 0) e = cudaEventRecord(ready, ks[0]);
         FusedParams fp{};
@@ -952,6 +937,10 @@ impir_status impir_answer_streamed(const void* records, uint64_t N, uint32_t B, 
         fp.bits_words = 1u << cfg.lane_bits;
         fp.rec_lo = lo;
         std::memcpy(fp.mmo_rk, dev->mmo_rk, sizeof fp.mmo_rk);
+        fp.bounds = sp.bounds;
+        fp.db_words = bounds_db_words(cnt * words, words);
+        fp.keys_bytes = total;
+        fp.smem_bytes = uint32_t(smem_for(cfg));
         if (e == cudaSuccess)
             e = launch_fused(cfg.queries_per_warp, nk_xor(words, cfg.queries_per_warp), dim3(dev->sms),
                              dim3(cfg.warps_per_cta * 32),
@@ -970,6 +959,7 @@ impir_status impir_answer_streamed(const void* records, uint64_t N, uint32_t B, 
         zp.n_queries = n;
         zp.record_bytes = B;
         zp.stride = stride;
+        zp.bounds = bounds_record();
         e = launch_finalize(zp, ks[0]);
         count_launches(1);
     }
@@ -983,7 +973,7 @@ impir_status impir_answer_streamed(const void* records, uint64_t N, uint32_t B, 
         X.zeroed_stride = 0;
         st = cuda_fail(e, "streamed answer");
     }
-    return st;
+    return st == IMPIR_OK ? bounds_verdict() : st;
 }
 
 // ---- tuning cache on disk ----

@@ -36,13 +36,15 @@ struct NoallocDevice {
     uint32_t* te0 = nullptr;      // device address of g_noalloc_te0 on this device
     int sms = 0;
     uint32_t mmo_rk[2][44];
+    BoundsRecord* bounds = nullptr;  // debug build: the device's record of failed index checks
 };
 
 std::mutex g_mu;
 NoallocDevice g_dev[kMaxDevices];
 
 // One-time set-up for the current device: look up the arrays' device addresses (host code
-// must not use the symbols themselves as addresses), fill the T-table, read the SM count.
+// must not use the symbols themselves as addresses), fill the T-table, read the SM count, and
+// prepare every kernel the entry point launches.
 impir_status device_setup(NoallocDevice** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return set_error(IMPIR_ECUDA, "no current CUDA device");
@@ -66,16 +68,17 @@ impir_status device_setup(NoallocDevice** out) {
             return set_error(IMPIR_ECUDA, "SM count query failed");
         host_aes_expand(reinterpret_cast<const uint8_t*>(IMPIR_MMO_KEY0), d.mmo_rk[0]);
         host_aes_expand(reinterpret_cast<const uint8_t*>(IMPIR_MMO_KEY1), d.mmo_rk[1]);
+        // every kernel a later call can launch: shared-memory limit set and code loaded on this
+        // device now, so that no later call does first-use work
+        if (prepare_xor_kernels() != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(IMPIR_ECUDA, "kernel preparation failed");
+        }
+        d.bounds = bounds_record();
         d.ready = true;
     }
     *out = &d;
     return IMPIR_OK;
-}
-
-uint32_t nk_words(uint32_t words) {
-    if (words <= 32) return 1;
-    const uint32_t need = (words + 31) / 32;
-    return need <= 2 ? 2 : need <= 4 ? 4 : 8;
 }
 
 }  // namespace
@@ -104,25 +107,12 @@ extern "C" impir_status impir_answer_noalloc(const void* d_records, uint64_t n_r
     if (impir_status s = device_setup(&dev)) return s;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
-    // launch shape: up to 8 queries per warp (16 accumulators per lane at most), the largest
-    // lane subtree that still gives every warp of the grid about three warp tiles
+    // launch shape: the asynchronous path's default for this database and batch
     const uint32_t words = stride_bytes / 16;
-    const uint32_t nk = nk_words(words);
-    uint32_t qpw = 8;
-    while (qpw > 1 && (qpw * nk > 16 || qpw > n_queries)) qpw >>= 1;
-    const uint32_t warps = 16;
-    const double groups = double((n_queries + qpw - 1) / qpw);
-    uint32_t lane_bits = 0;
-    for (int s = 8; s >= 0; --s) {
-        const size_t smem = kTableBytes + kSegSmemBytes + size_t(warps) * qpw * (size_t(1) << s) * 4;
-        if (smem > 227 * 1024) continue;
-        const double tiles = double((n_records + (32ull << s) - 1) / (32ull << s));
-        if (groups * tiles >= 3.0 * dev->sms * warps || s == 0) {
-            lane_bits = uint32_t(s);
-            break;
-        }
-    }
-    const size_t smem = kTableBytes + kSegSmemBytes + size_t(warps) * qpw * (size_t(1) << lane_bits) * 4;
+    const impir_config cfg = default_config(n_records, words, n_queries, dev->sms);
+    const uint32_t qpw = cfg.queries_per_warp, lane_bits = cfg.lane_bits;
+    const uint32_t nk = nk_xor(words, qpw);
+    const size_t smem = smem_for(cfg);
 
     SetupParams sp{};
     sp.keys = d_keys;
@@ -134,6 +124,7 @@ extern "C" impir_status impir_answer_noalloc(const void* d_records, uint64_t n_r
     sp.words = words;
     sp.lane_bits = lane_bits;
     sp.qpw = qpw;
+    sp.bounds = dev->bounds;
     if (launch_setup(sp, st) != cudaSuccess) {
         cudaGetLastError();
         return set_error(IMPIR_ECUDA, "setup kernel launch failed");
@@ -153,7 +144,10 @@ extern "C" impir_status impir_answer_noalloc(const void* d_records, uint64_t n_r
     fp.bits_words = 1u << lane_bits;
     for (int x = 0; x < 2; ++x)
         for (int i = 0; i < 44; ++i) fp.mmo_rk[x][i] = dev->mmo_rk[x][i];
-    if (launch_fused(qpw, nk, dim3(dev->sms), dim3(warps * 32), smem, st, fp) != cudaSuccess) {
+    fp.bounds = dev->bounds;
+    fp.db_words = bounds_db_words(n_records * words, words);
+    fp.smem_bytes = uint32_t(smem);
+    if (launch_fused(qpw, nk, dim3(dev->sms), dim3(cfg.warps_per_cta * 32), smem, st, fp) != cudaSuccess) {
         cudaGetLastError();
         return set_error(IMPIR_ECUDA, "fused kernel launch failed");
     }
@@ -165,6 +159,7 @@ extern "C" impir_status impir_answer_noalloc(const void* d_records, uint64_t n_r
     zp.n_queries = n_queries;
     zp.record_bytes = record_bytes;
     zp.stride = stride_bytes;
+    zp.bounds = dev->bounds;
     if (launch_finalize(zp, st) != cudaSuccess) {
         cudaGetLastError();
         return set_error(IMPIR_ECUDA, "finalize kernel launch failed");

@@ -9,9 +9,17 @@
 //
 // finalize_kernel copies each query's accumulator (record stride) into the caller's
 // answer buffer (record_bytes per query).
+#include <cstdlib>
+
+#include "bounds.cuh"
 #include "impir_internal.h"
 
 namespace impir {
+
+#ifdef IMPIR_BOUNDS
+// The per-device record of failed index checks (debug build).
+static __device__ BoundsRecord g_bounds_rec;
+#endif
 
 __global__ void __launch_bounds__(1024) setup_kernel(const SetupParams S) {
     __shared__ uint32_t hist[kMaxDomainBits + 1], cursor[kMaxDomainBits + 1];
@@ -29,6 +37,10 @@ __global__ void __launch_bounds__(1024) setup_kernel(const SetupParams S) {
     if (tid == 0) {
         s_nbad = 0;
         s_first_bad = 0xffffffffu;
+        hdr->bounds_failed = 0;
+#ifdef IMPIR_BOUNDS
+        s_bctx = BoundsCtx{S.bounds, hdr, S.keys, S.keys_bytes, nullptr, 0, 0, 0};
+#endif
     }
     __syncthreads();
 
@@ -37,6 +49,7 @@ __global__ void __launch_bounds__(1024) setup_kernel(const SetupParams S) {
         const uint32_t off = S.key_off[q];
         bool ok = (off & 7u) == 0;
         uint32_t m = 0;
+        if (ok && !IMPIR_IN_BOUNDS(S.keys_bytes == 0 || off + 8ull <= S.keys_bytes, kSiteKey, off)) ok = false;
         if (ok) {
             const uint8_t* k = S.keys + off;
             const uint2 h = *reinterpret_cast<const uint2*>(k);
@@ -46,6 +59,10 @@ __global__ void __launch_bounds__(1024) setup_kernel(const SetupParams S) {
             if (ok) {
                 const size_t z[3] = {8 + size_t(m + 1) * 16, 8 + size_t(m + 1) * 32, 8 + size_t(m + 1) * 48};
                 for (int i = 0; i < 3; ++i) {
+                    if (!IMPIR_IN_BOUNDS(S.keys_bytes == 0 || off + z[i] + 16 <= S.keys_bytes, kSiteKey, off + z[i])) {
+                        ok = false;
+                        break;
+                    }
                     const uint2* p = reinterpret_cast<const uint2*>(k + z[i]);
                     const uint2 a = p[0], b = p[1];
                     ok = ok && (a.x | a.y | b.x | b.y) == 0;
@@ -84,6 +101,7 @@ __global__ void __launch_bounds__(1024) setup_kernel(const SetupParams S) {
             const unsigned long long n_eff = S.n_records < dom ? S.n_records : dom;
             const unsigned long long tiles = m >= 5 + S.lane_bits ? (n_eff + tbig - 1) / tbig : 1ull;
             if (tiles > prev) {
+                if (!IMPIR_IN_BOUNDS(nseg < kMaxSegments, kSiteWorkspace, nseg)) break;
                 const uint32_t gcum = gstart[m] + ngrp[m];  // groups with domain bits >= m
                 // clip to the tiles this launch covers (a chunk of a streamed database)
                 const unsigned long long lo = prev > S.tile_lo ? prev : S.tile_lo;
@@ -113,7 +131,10 @@ __global__ void __launch_bounds__(1024) setup_kernel(const SetupParams S) {
     //    answers are independent of which queries share a group)
     for (uint32_t q = tid; q < S.n_queries; q += nthr) {
         const uint32_t m = qm[q];
-        if (m) perm[bstart[m] + atomicAdd(&cursor[m], 1u)] = q;
+        if (m) {
+            const uint32_t i = bstart[m] + atomicAdd(&cursor[m], 1u);
+            if (IMPIR_IN_BOUNDS(i < S.n_queries, kSiteWorkspace, i)) perm[i] = q;
+        }
     }
     // 4. group descriptors
     for (uint32_t gi = tid; gi < s_ngroups; gi += nthr) {
@@ -125,7 +146,7 @@ __global__ void __launch_bounds__(1024) setup_kernel(const SetupParams S) {
         d.count = min(S.qpw, hist[m] - k * S.qpw);
         d.m = m;
         d.pad = 0;
-        groups[gi] = d;
+        if (IMPIR_IN_BOUNDS(gi < S.n_queries + kMaxDomainBits + 8, kSiteWorkspace, gi)) groups[gi] = d;
     }
     // 5. zero the accumulators (kept across the chunks of a streamed database)
     if (!S.keep_acc) {
@@ -135,12 +156,44 @@ __global__ void __launch_bounds__(1024) setup_kernel(const SetupParams S) {
 }
 
 __global__ void finalize_kernel(const FinalizeParams F) {
+#ifdef IMPIR_BOUNDS
+    if (threadIdx.x == 0) s_bctx = BoundsCtx{F.bounds, nullptr, nullptr, 0, nullptr, 0, 0, 0};
+    __syncthreads();
+#endif
     const uint8_t* acc = F.ws + F.lay.off_acc;
     const size_t n = size_t(F.n_queries) * F.record_bytes;
     for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
         const size_t q = i / F.record_bytes, b = i - q * F.record_bytes;
-        F.out[i] = acc[q * F.stride + b];
+        const size_t a = q * F.stride + b;
+        if (IMPIR_IN_BOUNDS(b < F.stride && a < size_t(F.n_queries) * F.stride, kSiteAcc, a)) F.out[i] = acc[a];
     }
+}
+
+BoundsRecord* bounds_record() {
+#ifdef IMPIR_BOUNDS
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_bounds_rec) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return static_cast<BoundsRecord*>(p);
+#else
+    return nullptr;
+#endif
+}
+
+unsigned long long bounds_db_words(unsigned long long n_words, uint32_t words_per_record) {
+#ifdef IMPIR_BOUNDS
+    // a debug-build test withholds the last records of every database from the checked extent
+    // (the memory stays valid), so that the checks on record reads fire
+    if (const char* w = std::getenv("IMPIR_BOUNDS_TEST_WITHHOLD_RECORDS")) {
+        const unsigned long long k = std::strtoull(w, nullptr, 10) * words_per_record;
+        return k < n_words ? n_words - k : 0;
+    }
+#else
+    (void)words_per_record;
+#endif
+    return n_words;
 }
 
 cudaError_t launch_setup(const SetupParams& p, cudaStream_t s) {
@@ -165,6 +218,18 @@ cudaError_t launch_fused(uint32_t qpw, uint32_t nk, dim3 grid, dim3 block, size_
         case 16: return launch_fused_q16(nk, grid, block, smem, s, p);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t prepare_xor_kernels() {
+    cudaError_t e = prepare_fused_q1();
+    if (e == cudaSuccess) e = prepare_fused_q2();
+    if (e == cudaSuccess) e = prepare_fused_q4();
+    if (e == cudaSuccess) e = prepare_fused_q8();
+    if (e == cudaSuccess) e = prepare_fused_q16();
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, setup_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, finalize_kernel);
+    return e;
 }
 
 }  // namespace impir

@@ -25,3 +25,14 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(autouse=True)
+def _bounds_checks_clean(request):
+    """With the debug library loaded (IMPIR_BOUNDS=1), every GPU test must end with no failed
+    index check in the kernels it ran."""
+    yield
+    if os.environ.get("IMPIR_BOUNDS") == "1" and request.node.get_closest_marker("gpu"):
+        import paper_2509_06514_gb300 as impir
+        st = impir.impir_bounds_status()
+        assert st["n_failed"] == 0, f"failed index checks: {st}"
