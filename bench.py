@@ -43,6 +43,9 @@ def parse_args():
     p.add_argument("--queries", type=int, default=None, help="query count of the batched256m workload (default 64)")
     p.add_argument("--record-bytes", type=int, default=None,
                    help="record size of the batched4g workload (a power of two; N = 4 GiB / record size)")
+    p.add_argument("--db-log2", type=int, default=None,
+                   help="database of 2^k bytes for the uneven8g / batched4g workloads (same batches; small "
+                        "profiling cases)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true", help="skip the one-query-per-launch comparison")
     p.add_argument("--no-tune", action="store_true")
@@ -59,12 +62,16 @@ def parse_args():
     return p.parse_args()
 
 
-def make_workload(name, queries=None, record_bytes=None):
+def make_workload(name, queries=None, record_bytes=None, db_log2=None):
+    """The named workload; db_log2 shrinks the uneven or 4 GiB workload's database to 2^db_log2
+    bytes with the same batches (profiling captures of a small case)."""
     from paper_2509_06514_gb300 import workloads as W
     if name == "batched256m" and queries:
         return W.batched_256mib(n_queries=queries)
-    if name == "batched4g" and record_bytes:
-        return W.batched_4gib(record_bytes=record_bytes)
+    if name == "batched4g" and (record_bytes or db_log2):
+        return W.batched_4gib(record_bytes=record_bytes or 1024, db_bytes=1 << (db_log2 or 32))
+    if name == "uneven8g" and db_log2:
+        return W.uneven_8gib(log2n=db_log2 - 8)
     return {"uneven8g": W.uneven_8gib, "batched4g": W.batched_4gib, "batched256m": W.batched_256mib,
             "single": W.single_query}[name]()
 
@@ -240,7 +247,7 @@ def run_reference(args, world, rank):
     import oracle
     from paper_2509_06514_gb300 import workloads
     oracle.build()
-    w = make_workload(args.workload, args.queries, args.record_bytes)
+    w = make_workload(args.workload, args.queries, args.record_bytes, args.db_log2)
     cores = os.cpu_count() or 1
     # one query per step, taken round-robin from the workload (records regenerated once)
     db = workloads.make_db(w.n_records, w.record_bytes, w.db_seed)
@@ -397,7 +404,7 @@ def main():
     if args.calibrate_only:
         print(json.dumps(calibrate_engines(impir)), flush=True)
         return
-    w = make_workload(args.workload, args.queries, args.record_bytes)
+    w = make_workload(args.workload, args.queries, args.record_bytes, args.db_log2)
     N, B = w.n_records, w.record_bytes
     t_setup = time.perf_counter()
     db = workloads.make_db(N, B, w.db_seed)

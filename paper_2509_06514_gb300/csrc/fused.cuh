@@ -671,6 +671,18 @@ __device__ __forceinline__ void acc_xor(const FusedParams& P, uint4* acc_out, ui
     red_xor(acc_out + size_t(qi) * P.words + k, v);
 }
 
+// All-ones if bit 31 of x is set, else zero, as the high word of the signed product x * one
+// (one == 1 at run time): an integer multiply (FMA pipe) instead of an arithmetic shift (ALU pipe).
+__device__ __forceinline__ uint32_t sign_mask_fma(uint32_t x, uint32_t one) {
+    uint32_t m;
+    asm("mul.hi.s32 %0, %1, %2;" : "=r"(m) : "r"(x), "r"(one));
+    return m;
+}
+
+__device__ __forceinline__ uint4 bxor3(const uint4 a, const uint4 b, const uint4 c) {
+    return make_uint4(a.x ^ b.x ^ c.x, a.y ^ b.y ^ c.y, a.z ^ b.z ^ c.z, a.w ^ b.w ^ c.w);
+}
+
 __device__ __forceinline__ void xor_masked(uint4& a, const uint4 v, uint32_t msk) {
     a.x ^= v.x & msk;
     a.y ^= v.y & msk;
@@ -713,13 +725,20 @@ __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_ba
             for (int q = 0; q < QC; ++q) sel[q] = ld_slice(&bits[q * bw + (c0 >> 5)]) >> lr;  // bit i*R: record c0+i*R+lr
             const uint32_t nloc = min(32u, nrec - c0);
             if (R == 1) {
-                // one record per step for the whole warp: its selection bits are warp-uniform
-#pragma unroll 4
-                for (uint32_t i = 0; i < nloc; ++i) {
-                    const uint4 v = on ? ld_db(base + size_t(c0 + i) * W) : make_uint4(0, 0, 0, 0);
+                // one record per step for the whole warp: its selection bits are warp-uniform;
+                // four records' loads in flight, one bit mask per record shared by the queries
+                for (uint32_t i0 = 0; i0 < nloc; i0 += 4) {
+                    uint4 v[4];
 #pragma unroll
-                    for (int q = 0; q < QC; ++q)
-                        if ((sel[q] >> i) & 1u) acc[q] = bxor4(acc[q], v);
+                    for (int u = 0; u < 4; ++u)
+                        v[u] = (on && i0 + u < nloc) ? ld_db(base + size_t(c0 + i0 + u) * W) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t bm = 1u << (i0 + u);
+#pragma unroll
+                        for (int q = 0; q < QC; ++q)
+                            if (sel[q] & bm) acc[q] = bxor4(acc[q], v[u]);
+                    }
                 }
             } else {
                 // bit-reversed selection words: step i's bit sits in bit 31 of sh << i, so a step
@@ -761,39 +780,81 @@ __device__ __forceinline__ void scan_tile(const FusedParams& P, uint64_t tile_ba
         }
     } else {
         // W > 32: the whole warp reads one record per step, NK words per lane, in column
-        // passes; a record's selection bits are warp-uniform, so unselected records skip the XOR
+        // passes; a record's selection bits are warp-uniform. The compiler predicates a
+        // conditional XOR of this size rather than branching (and real branches measured slower),
+        // so every query costs ALU work on every record either way. With NK = 2 the XOR is masked,
+        // the mask taken on the FMA pipe; with NK >= 4 two records are taken together, both selected
+        // costing one 3-input XOR.
+        const uint32_t one = P.n_queries != 0 ? 1u : 0u;  // 1, opaque to the compiler
+        constexpr int RB = NK <= 2 ? 4 : NK == 4 ? 2 : 1;  // records' loads in flight per lane
         for (uint32_t k0 = 0; k0 < W; k0 += 32 * NK) {
             uint4 acc[QC][NK];
 #pragma unroll
             for (int q = 0; q < QC; ++q)
 #pragma unroll
                 for (int c = 0; c < NK; ++c) acc[q][c] = make_uint4(0, 0, 0, 0);
+            // this lane's words of the tile's records in this pass: record r, column c at
+            // tb + r * W + 32 * c
+            const uint4* tb = P.db + (tile_base - P.rec_lo) * W + k0 + lane;
+            bool kon[NK];
+#pragma unroll
+            for (int c = 0; c < NK; ++c) kon[c] = k0 + lane + 32 * c < W;
             for (uint32_t c0 = 0; c0 < nrec; c0 += 32) {
                 uint32_t sel[QC];
 #pragma unroll
                 for (int q = 0; q < QC; ++q) sel[q] = ld_slice(&bits[q * bw + (c0 >> 5)]);
                 const uint32_t nloc = min(32u, nrec - c0);
-                // RB records' loads in flight before their XORs (fewer for the widest records,
-                // whose loads already fill the registers)
-                constexpr int RB = NK <= 2 ? 4 : NK == 4 ? 2 : 1;
+                const uint4* rp = tb + size_t(c0) * W;
+                uint32_t sh[QC];  // bit-reversed selection words (NK = 2): record i's bit in bit 31 of sh << i
+#pragma unroll
+                for (int q = 0; q < QC; ++q) sh[q] = __brev(sel[q]);
                 for (uint32_t i0 = 0; i0 < nloc; i0 += RB) {
                     uint4 v[RB][NK];
 #pragma unroll
-                    for (int u = 0; u < RB; ++u) {
-                        const uint4* rec = P.db + (tile_base - P.rec_lo + c0 + i0 + u) * W;
-#pragma unroll
-                        for (int c = 0; c < NK; ++c) {
-                            const uint32_t k = k0 + lane + 32 * c;
-                            v[u][c] = (k < W && i0 + u < nloc) ? ld_db(rec + k) : make_uint4(0, 0, 0, 0);
-                        }
-                    }
-#pragma unroll
                     for (int u = 0; u < RB; ++u)
 #pragma unroll
-                        for (int q = 0; q < QC; ++q)
-                            if ((sel[q] >> (i0 + u)) & 1u)
+                        for (int c = 0; c < NK; ++c)
+                            v[u][c] = (kon[c] && i0 + u < nloc) ? ld_db(rp + size_t(i0 + u) * W + 32 * c)
+                                                                : make_uint4(0, 0, 0, 0);
+                    if constexpr (NK <= 2) {
 #pragma unroll
-                                for (int c = 0; c < NK; ++c) acc[q][c] = bxor4(acc[q][c], v[u][c]);
+                        for (int u = 0; u < RB; ++u)
+#pragma unroll
+                            for (int q = 0; q < QC; ++q) {
+                                const uint32_t msk = sign_mask_fma(sh[q], one);
+#pragma unroll
+                                for (int c = 0; c < NK; ++c) xor_masked(acc[q][c], v[u][c], msk);
+                                asm("mul.lo.u32 %0, %0, %1;" : "+r"(sh[q]) : "r"(one << 1));
+                            }
+                    } else if constexpr (RB >= 2) {
+#pragma unroll
+                        for (int u = 0; u < RB; u += 2) {
+                            const uint32_t b0 = 1u << (i0 + u), b1 = b0 << 1;
+#pragma unroll
+                            for (int q = 0; q < QC; ++q) {
+                                const uint32_t sq = sel[q];
+                                if (sq & b0) {
+                                    if (sq & b1) {
+#pragma unroll
+                                        for (int c = 0; c < NK; ++c) acc[q][c] = bxor3(acc[q][c], v[u][c], v[u + 1][c]);
+                                    } else {
+#pragma unroll
+                                        for (int c = 0; c < NK; ++c) acc[q][c] = bxor4(acc[q][c], v[u][c]);
+                                    }
+                                } else if (sq & b1) {
+#pragma unroll
+                                    for (int c = 0; c < NK; ++c) acc[q][c] = bxor4(acc[q][c], v[u + 1][c]);
+                                }
+                            }
+                        }
+                    } else {
+                        const uint32_t bm = 1u << i0;
+#pragma unroll
+                        for (int q = 0; q < QC; ++q)
+                            if (sel[q] & bm)
+#pragma unroll
+                                for (int c = 0; c < NK; ++c) acc[q][c] = bxor4(acc[q][c], v[0][c]);
+                    }
                 }
             }
 #pragma unroll

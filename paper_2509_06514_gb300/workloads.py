@@ -135,11 +135,11 @@ def batched_256mib(seed: int = 1, n_queries: int = 64) -> Workload:
     return w
 
 
-def batched_4gib(seed: int = 2, record_bytes: int = 1024) -> Workload:
-    """Batched GB-scale: 4 GiB of records of record_bytes (a power of two; default 1 KiB:
-    N=2^22), 256 queries whose domain covers the DB (m = log2 N)."""
+def batched_4gib(seed: int = 2, record_bytes: int = 1024, db_bytes: int = 4 << 30) -> Workload:
+    """Batched GB-scale: 4 GiB (db_bytes) of records of record_bytes (a power of two; default
+    1 KiB: N=2^22), 256 queries whose domain covers the DB (m = log2 N)."""
     assert record_bytes > 0 and record_bytes & (record_bytes - 1) == 0
-    n = (4 << 30) // record_bytes
+    n = db_bytes // record_bytes
     m = log2_exact(n)
     rng = np.random.default_rng(seed)
     name = (f"batched: N=2^{m} x {record_bytes // 1024} KiB, m={m}, Q=256" if record_bytes >= 1024
@@ -149,17 +149,19 @@ def batched_4gib(seed: int = 2, record_bytes: int = 1024) -> Workload:
     return w
 
 
-def uneven_8gib(seed: int = 3, n_queries: int = 1024, max_batch: int = 512) -> Workload:
+def uneven_8gib(seed: int = 3, n_queries: int = 1024, max_batch: int = 512, log2n: int = 25) -> Workload:
     """Batched uneven: N=2^25 x 256 B (8 GiB); n_queries split into batches of uniform
     size 1..max_batch (the last one truncated), domains mixed over 2^23, 2^24, 2^25, each
-    query against the DB prefix its domain covers."""
+    query against the DB prefix its domain covers. log2n < 25 gives the same batch sizes over a
+    smaller database (N = 2^log2n, domains 2^(log2n-2) .. 2^log2n), for profiling captures."""
     rng = np.random.default_rng(seed)
-    w = Workload(f"uneven: N=2^25 x 256 B, m in {{23,24,25}}, {n_queries} queries in batches of 1..{max_batch}",
-                 1 << 25, 256, seed)
+    mset = [log2n - 2, log2n - 1, log2n]
+    w = Workload(f"uneven: N=2^{log2n} x 256 B, m in {{{','.join(map(str, mset))}}}, {n_queries} queries in "
+                 f"batches of 1..{max_batch}", 1 << log2n, 256, seed)
     q = 0
     while q < n_queries:
         n = min(int(rng.integers(1, max_batch + 1)), n_queries - q)
-        ms = rng.choice([23, 24, 25], size=n)
+        ms = rng.choice(mset, size=n)
         w.batches.append(_batch(rng, n, ms, w.n_records, seed + 1000, q))
         q += n
     return w
