@@ -174,7 +174,8 @@ def kernel_source_hash() -> str:
     import hashlib
     import re
     h = hashlib.sha256()
-    for f in ("fused.cuh", "fused_q1.cu", "fused_q2.cu", "fused_q4.cu", "fused_q8.cu", "setup.cu"):
+    for f in ("fused.cuh", "bounds.cuh", "impir_internal.h", "fused_q1.cu", "fused_q2.cu", "fused_q4.cu", "fused_q8.cu",
+              "fused_q16.cu", "setup.cu"):
         with open(os.path.join(ROOT, "paper_2509_06514_gb300", "csrc", f)) as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
@@ -183,17 +184,27 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
-def captured_traffic(cfg: dict, workload: str):
-    """DRAM bytes per fused launch from the committed ncu capture of this workload, if that
-    capture was taken on the current kernel source with the same launch shape; else None."""
+def captured_traffic(cfg: dict, batches: list):
+    """DRAM bytes per fused launch of this step, from the committed ncu capture of the same
+    batches on a smaller database (1 GiB; the full-size workload is too large to capture with
+    more than the launch-time metric): each batch's measured DRAM bytes per byte of the DB prefix
+    its queries cover, times that prefix here, averaged over the step's launches. Valid only for
+    the kernel source and launch shape the capture was taken with; else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "fused_kernel_traffic.json")) as f:
             t = json.load(f)
     except OSError:
         return None
-    if t.get("kernel_source_sha256") != kernel_source_hash() or t.get("launch") != cfg or t.get("workload") != workload:
+    if t.get("kernel_source_sha256") != kernel_source_hash() or t.get("launch") != cfg:
         return None
-    return t.get("dram_bytes_per_launch")
+    per = t.get("per_batch", [])
+    if [b["queries"] for b in per] != [bt["n"] for bt in batches]:
+        return None
+    total = 0.0
+    for b, bt in zip(per, batches):
+        ratio = (b["dram_read_bytes"] + b["dram_write_bytes"]) / b["db_prefix_bytes"]
+        total += ratio * bt["prefix_bytes"]
+    return total / len(per)
 
 
 def peaks():
@@ -374,16 +385,24 @@ def run_serving(args, impir, workloads):
 # ---------------------------------------------------------------- AES engine calibration
 
 def calibrate_engines(impir, iters: int = 2000):
-    """The fused kernel's AES engine alone (no tree walk, no scan): every thread of one CTA of
-    512 per SM iterates a node expansion (two AES blocks) in registers; both PRFs."""
+    """The AES engines alone (no tree walk, no scan), each thread iterating node expansions
+    (two AES blocks each) in registers: the fused kernel's T-table engine with one CTA of 512
+    threads per SM, both PRFs, and the bitsliced engine (fixed-key PRF only) with 256 threads of
+    16 seeds each per SM. G AES blocks per second of device time."""
     sms = impir.impir_device_sm_count()
     n = sms * 512
     seeds = np.random.default_rng(7).integers(0, 256, (n, 16), dtype=np.uint8)
     out = {}
-    for prf, name in ((impir.IMPIR_PRF_AES_KEYED, "keyed"), (impir.IMPIR_PRF_AES_MMO, "mmo")):
+    for prf, name in ((impir.IMPIR_PRF_AES_KEYED, "ttable_keyed"), (impir.IMPIR_PRF_AES_MMO, "ttable_mmo")):
         _, ms = impir.impir_aes_calibrate(prf, iters, seeds, 512)
         out[name] = {"gaes_per_s": 2 * iters * n / (ms / 1e3) / 1e9, "ms": ms, "blocks": 2 * iters * n}
-    return {"calibration": out, "threads": n, "iters": iters}
+    nb = sms * 256
+    bseeds = np.random.default_rng(8).integers(0, 256, (nb * 16, 16), dtype=np.uint8)
+    biters = max(1, iters // 16)
+    _, ms = impir.impir_aes_calibrate_bitsliced(biters, bseeds, 256)
+    out["bitsliced_mmo"] = {"gaes_per_s": 2 * biters * 16 * nb / (ms / 1e3) / 1e9, "ms": ms,
+                            "blocks": 2 * biters * 16 * nb}
+    return out
 
 
 # ---------------------------------------------------------------- our arm
@@ -402,7 +421,7 @@ def main():
     torch.cuda.set_device(local)
     build.build()
     if args.calibrate_only:
-        print(json.dumps(calibrate_engines(impir)), flush=True)
+        print(json.dumps({"calibration": calibrate_engines(impir)}), flush=True)
         return
     w = make_workload(args.workload, args.queries, args.record_bytes, args.db_log2)
     N, B = w.n_records, w.record_bytes
@@ -426,6 +445,7 @@ def main():
         wsb = impir.impir_workspace_bytes(n, stride)
         batches.append({
             "n": n, "ms": list(b.ms), "alphas": list(b.alphas), "blob0": blob0, "blob1": blob1,
+            "prefix_bytes": max(min(N, 1 << m) for m in b.ms) * stride,
             "d_keys0": torch.from_numpy(np.frombuffer(blob0, np.uint8).copy()).cuda(),
             "d_keys1": torch.from_numpy(np.frombuffer(blob1, np.uint8).copy()).cuda(),
             "d_off": torch.from_numpy(offs.view(np.int32).copy()).cuda(),
@@ -569,17 +589,16 @@ def main():
                         f"engine {ac['engine_alu_thread_inst_per_block']:.1f} ALU ops per block "
                         f"({ac['source']})"}
 
-    # AES engine alone (same device code, no tree walk / scan): the ceiling the fused kernel
-    # approaches; its lookup rate shows how close the engine runs to the shared-memory port
-    rs = np.random.default_rng(7)
-    n_cal = sms * 512
-    _, cal_ms = impir.impir_aes_calibrate(impir.IMPIR_PRF_AES_KEYED, 2000,
-                                          rs.integers(0, 256, (n_cal, 16), dtype=np.uint8), 512)
-    engine_gaes = 2 * 2000 * n_cal / (cal_ms / 1e3) / 1e9
+    # AES engines alone (no tree walk / scan): the ceiling the fused kernel approaches, and the
+    # bitsliced alternative; the T-table engine's lookup rate shows how close it runs to the port
+    cal = calibrate_engines(impir)
+    engine_gaes = cal["ttable_keyed"]["gaes_per_s"]
     engine = {"gaes_per_s": engine_gaes,
               "lookups_per_clk_per_sm": engine_gaes * 1e9 * LOOKUPS_INTERNAL_PAIR / 2 / (sms * mhz * 1e6),
               "fused_over_engine": (achieved / engine_gaes) if achieved else None,
-              "note": "keyed node expansions in registers, 172.5 table lookups per block (round 1 shared)"}
+              "engines": {k: v["gaes_per_s"] for k, v in cal.items()},
+              "note": "keyed T-table node expansions in registers, 172.5 table lookups per block (round 1 "
+                      "shared); bitsliced engine: fixed-key PRF, 154-gate S-box circuit, no lookups"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -793,7 +812,7 @@ def main():
         serving = run_serving(args, impir, workloads)
 
     if rank == 0:
-        traffic = captured_traffic(cfg, w.name)
+        traffic = captured_traffic(cfg, batches)
         out = {
             "metric": "PIR queries/s (DPF eval+dpXOR) at 8 GiB DB", "value": value, "unit": "queries/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

@@ -372,6 +372,17 @@ impir_status impir_timing_read(double* fused_ms, uint64_t* fused_launches, uint6
 impir_status impir_aes_calibrate(int prf, uint32_t iters, uint32_t n_threads, uint32_t threads_per_cta,
                                  const uint8_t* seeds, uint8_t* out, double* ms);
 
+/* Bitsliced AES calibration (measurement support; the paper has no counterpart): the same
+ * iteration p <- PRF_p(0) XOR PRF_p(1) for the fixed-key PRF (IMPIR_PRF_AES_MMO), computed by an
+ * engine with no table lookups: AES on bit-slices, each thread carrying 16 seeds under both keys
+ * in 32-bit words (one logic operation advances 32 AES computations; the S-box is a 154-gate
+ * composite-field circuit). seeds: n_threads * 16 seeds of 16 bytes (host), thread g taking seeds
+ * 16g .. 16g + 15; out receives the final states in the same layout; *ms the device time of the
+ * timed launch (2 * iters * 16 * n_threads AES-128 blocks). threads_per_cta: a multiple of 32,
+ * <= 256. Allocates and frees its own device buffers. */
+impir_status impir_aes_calibrate_bitsliced(uint32_t iters, uint32_t n_threads, uint32_t threads_per_cta,
+                                           const uint8_t* seeds, uint8_t* out, double* ms);
+
 /* Index checks of the debug build (measurement and test support; the paper has no
  * counterpart). A library compiled with IMPIR_BOUNDS (libimpir_bounds.so, built by
  * `python -m paper_2509_06514_gb300.build --bounds`) compares every shared-memory, database

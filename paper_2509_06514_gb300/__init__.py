@@ -37,7 +37,7 @@ EXPORTS = [
     "impir_aes_calibrate", "impir_db_update", "impir_db_update_async", "impir_db_version", "impir_server_update",
     "impir_answer_streamed", "impir_answer_add32", "impir_answer_add32_async", "impir_tune_cache_save",
     "impir_tune_cache_load", "impir_db_load_rows", "impir_db_rows", "impir_combine_partials",
-    "impir_get_config_add32", "impir_bounds_status",
+    "impir_get_config_add32", "impir_bounds_status", "impir_aes_calibrate_bitsliced",
 ]
 
 
@@ -134,6 +134,8 @@ def lib():
                 "impir_combine_partials": (ctypes.c_int, [ctypes.c_int, vp, ctypes.c_uint32, ctypes.c_uint64, vp, vp]),
                 "impir_bounds_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
                                                        ctypes.POINTER(ctypes.c_uint64)]),
+                "impir_aes_calibrate_bitsliced": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                                                 u8p, u8p, ctypes.POINTER(ctypes.c_double)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -430,6 +432,20 @@ def impir_aes_calibrate(prf: int, iters: int, seeds: np.ndarray, threads_per_cta
     ms = ctypes.c_double()
     _check(lib().impir_aes_calibrate(prf, iters, sd.shape[0], threads_per_cta, ctypes.c_void_p(sd.ctypes.data),
                                      ctypes.c_void_p(out.ctypes.data), ctypes.byref(ms)), "impir_aes_calibrate")
+    return out, ms.value
+
+
+def impir_aes_calibrate_bitsliced(iters: int, seeds: np.ndarray, threads_per_cta: int = 256):
+    """Bitsliced engine run (fixed-key PRF): seeds (16 n, 16) uint8, 16 per thread; returns
+    (final states (16 n, 16) uint8, device ms)."""
+    sd = np.ascontiguousarray(seeds, dtype=np.uint8).reshape(-1, 16)
+    if sd.shape[0] % 16:
+        raise ValueError("the bitsliced engine takes 16 seeds per thread")
+    out = np.zeros_like(sd)
+    ms = ctypes.c_double()
+    _check(lib().impir_aes_calibrate_bitsliced(iters, sd.shape[0] // 16, threads_per_cta,
+                                               ctypes.c_void_p(sd.ctypes.data), ctypes.c_void_p(out.ctypes.data),
+                                               ctypes.byref(ms)), "impir_aes_calibrate_bitsliced")
     return out, ms.value
 
 
