@@ -683,13 +683,17 @@ def main():
             al.append(bt["alphas"][i])
         b0, b1 = b"".join(k0s), b"".join(k1s)
         impir.impir_answer_add32(dbh, b0, len(sub), B)            # warm
-        t0 = time.perf_counter()
-        a0 = impir.impir_answer_add32(dbh, b0, len(sub), B)
-        t_add = time.perf_counter() - t0
-        a1 = impir.impir_answer_add32(dbh, b1, len(sub), B)
-        t0 = time.perf_counter()
         impir.impir_answer(dbh, b0, len(sub), B)
-        t_xor = time.perf_counter() - t0
+        ta, tx = [], []
+        for _ in range(3):     # medians of three synchronous calls each
+            t0 = time.perf_counter()
+            a0 = impir.impir_answer_add32(dbh, b0, len(sub), B)
+            ta.append(time.perf_counter() - t0)
+            t0 = time.perf_counter()
+            impir.impir_answer(dbh, b0, len(sub), B)
+            tx.append(time.perf_counter() - t0)
+        t_add, t_xor = statistics.median(ta), statistics.median(tx)
+        a1 = impir.impir_answer_add32(dbh, b1, len(sub), B)
         s32 = (a0.view("<u4").astype(np.uint64) + a1.view("<u4").astype(np.uint64)) % (1 << 32)
         rec = s32.astype("<u4").view(np.uint8).reshape(len(sub), B)
         ok = sum(int(np.array_equal(rec[i], db[a])) for i, a in enumerate(al))
