@@ -260,9 +260,15 @@ def run_reference(args, world, rank):
     oracle.build()
     w = make_workload(args.workload, args.queries, args.record_bytes, args.db_log2)
     cores = os.cpu_count() or 1
-    # one query per step, taken round-robin from the workload (records regenerated once)
+    # one query per step, the workload's domain sizes taken in turn (so that a short run costs
+    # what the workload's mix costs), records regenerated once
     db = workloads.make_db(w.n_records, w.record_bytes, w.db_seed)
-    qs = [(m, a, s) for b in w.batches for m, a, s in zip(b.ms, b.alphas, b.seeds)]
+    by_m = {}
+    for b in w.batches:
+        for m, a, s in zip(b.ms, b.alphas, b.seeds):
+            by_m.setdefault(m, []).append((m, a, s))
+    order = sorted(by_m)
+    qs = [q for row in zip(*(by_m[m] for m in order)) for q in row]
     times = []
     for i in range(args.warmup + args.steps):
         m, a, s = qs[i % len(qs)]
@@ -281,7 +287,9 @@ def run_reference(args, world, rank):
         "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded uniform random records)",
         "config": {"workload": w.name, "step": "one query of the workload per step (bounded sample)"},
         "cpu_baseline": {"value": v, "unit": "queries/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} queries of the workload, one per step, threaded oracle"},
+                         "sample": f"{args.steps} queries of the workload, one per step, domain sizes in turn "
+                                   f"(m = {[qs[i % len(qs)][0] for i in range(args.warmup, args.warmup + args.steps)]}), "
+                                   f"threaded oracle"},
         "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
