@@ -427,6 +427,11 @@ def main():
     from paper_2509_06514_gb300 import build, workloads
 
     torch.cuda.set_device(local)
+    # one rank builds (the ranks share the source tree and its object files); the others find
+    # the library up to date after the barrier
+    if rank == 0:
+        build.build()
+    barrier(world)
     build.build()
     if args.calibrate_only:
         print(json.dumps({"calibration": calibrate_engines(impir)}), flush=True)
