@@ -394,7 +394,10 @@ impir_status impir_aes_calibrate_bitsliced(uint32_t iters, uint32_t n_threads, u
  * number of failed checks since the last call, the site code and index of the first one
  * (sites: 1 T-table, 2 selection-bit/node/share buffer, 3 database word, 4 key byte, 5 query
  * index, 6 schedule, 7 accumulator word, 8 lane stack, 9 setup writes, 10 answer byte), and
- * clears the record. EINVAL in a library built without IMPIR_BOUNDS. */
+ * clears the record. EINVAL in a library built without IMPIR_BOUNDS. For testing the checks
+ * themselves, the debug library reads IMPIR_BOUNDS_TEST_WITHHOLD_RECORDS=k from the environment
+ * and withholds the last k records of every database from the checked extent (their memory stays
+ * valid), so that reads of them fail the check; the normal library ignores it. */
 impir_status impir_bounds_status(uint32_t* n_failed, uint32_t* first_site, uint64_t* first_index);
 
 /* Number of streaming multiprocessors of the current device (0 if none). */

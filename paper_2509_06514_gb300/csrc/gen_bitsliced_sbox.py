@@ -187,12 +187,6 @@ def xor_network(c: Circuit, inputs: list[str], rows: list[int]) -> list[str]:
     return outs
 
 
-def count_xors(rows: list[int]) -> int:
-    c = Circuit()
-    xor_network(c, [f"i{i}" for i in range(8)], rows)
-    return len(c.ops)
-
-
 def gf16_mul_circuit(c: Circuit, a: list[str], b: list[str]) -> list[str]:
     """a * b in GF(16), bit lists LSB first: products a_i b_j reduced mod z^4 + z + 1."""
     terms: list[list[str]] = [[] for _ in range(4)]
